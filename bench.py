@@ -1,0 +1,386 @@
+"""Benchmark: GStencil/s and HBM-roofline fraction of the stencil sweep on GB300.
+
+One "step" is one full solve of the workload through the C ABI: the 2D radius-2
+box stencil (25 points) on an 8192 x 8192 FP32 grid, random normalised
+coefficients, periodic boundary, 100 time steps (stencil_apply with inputs
+resident in HBM).  The grid (256 MiB) is larger than L2, so no flush is needed
+between steps.  Beside it the line reports the CUDA-core gather form at equal
+error, the error of both against the FP64 oracle at sampled points, p50/p99,
+the roofline of the dominant kernel and the oracle's own speed on the host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own copy of the workload (independent
+problems, no data exchange: weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GStencil/s and % HBM roofline, matrixized vs gather at equal error; p50/p99"
+UNIT = "GStencil/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=8192)
+    ap.add_argument("--tsteps", type=int, default=100, help="stencil time steps per solve")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    import stencil_inputs as si
+    return si.box25_8192(args.dtype, args.tsteps, args.side)
+
+
+def workload_config(p, args, extra=None):
+    cfg = {"workload": f"2D box r=2 (25-point) {p.shape[0]}x{p.shape[1]} {args.dtype.upper()}, "
+                       f"periodic, {p.steps} time steps per solve, uniform[0,1) coefficients normalised to 1",
+           "grid": list(p.shape), "radius": p.r, "kind": p.kind, "boundary": p.bc,
+           "time_steps_per_solve": p.steps,
+           "l2_policy": "inputs larger than L2 (grid 256 MiB FP32 > 129 MB L2); no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_16298_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes for the kernel from the committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def oracle_baseline(p, field, max_seconds=20.0):
+    """Time the FP64 oracle on a bounded sample of the workload: the full grid,
+    as many whole time steps as fit in about max_seconds (at least one)."""
+    import oracle
+    oracle.build()
+    cores = oracle.threads()
+    t0 = time.perf_counter()
+    oracle.gather(field, p.r, p.coeffs, p.bc, 1)
+    t1 = time.perf_counter() - t0
+    nsteps = max(1, min(p.steps, int(max_seconds / max(t1, 1e-6)) - 1))
+    if nsteps > 1:
+        t0 = time.perf_counter()
+        oracle.gather(field, p.r, p.coeffs, p.bc, nsteps)
+        dt = time.perf_counter() - t0
+    else:
+        nsteps, dt = 1, t1
+    gst = p.points * nsteps / dt / 1e9
+    return {"value": gst, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full {p.shape[0]}x{p.shape[1]} grid, {nsteps} of {p.steps} time steps, "
+                      f"{dt:.1f} s, FP64 gather definition, OpenMP over rows"}
+
+
+def sample_points(shape, n=8, seed=77):
+    rng = np.random.default_rng(seed)
+    pts = np.stack([rng.integers(0, s, size=n) for s in shape], axis=1)
+    pts[0] = 0
+    pts[1] = np.array(shape) - 1
+    return pts
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import stencil_inputs as si
+    p = workload(args)
+    field = p.field()
+    # each "step" is a bounded sample: one time step of the full grid
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.gather(field, p.r, p.coeffs, p.bc, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.gather(field, p.r, p.coeffs, p.bc, 1)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    v = p.points / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(p, args, {"sample": "one time step of the full grid per bench step"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "one of the workload's time steps on the full grid per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    import paper_2310_16298_gb300 as sx
+    import stencil_inputs as si
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = workload(args)
+    field = p.field()
+    td = torch.float32 if p.dtype == "f32" else torch.float64
+    x = torch.tensor(field, dtype=td, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    results = {}
+    for impl in ("matrixized", "gather"):
+        try:
+            plan = sx.Plan(p.shape, p.r, p.kind, p.coeffs, p.dtype, bc=p.bc, impl=impl)
+        except sx.StencilError as e:
+            results[impl] = {"unavailable": str(e)}
+            continue
+        results[impl] = {"plan": plan}
+
+    main_impl = "matrixized" if "plan" in results.get("matrixized", {}) else "gather"
+
+    # accuracy of each implementation at sampled points (oracle on the dependency cone)
+    import oracle
+    pts = sample_points(p.shape)
+    want = oracle.sample(field, p.r, p.coeffs, p.bc, p.steps, pts) if rank == 0 else None
+    for impl, res in results.items():
+        if "plan" not in res:
+            continue
+        with torch.cuda.stream(stream):
+            res["plan"].apply(x, y, p.steps, stream)
+        stream.synchronize()
+        if rank == 0:
+            idx = tuple(torch.as_tensor(c, device=dev) for c in pts.T)
+            got = y[idx].double().cpu().numpy()
+            l2, mx = oracle.error_norms(got, want)
+            res["err"] = {"rel_l2": l2, "rel_max": mx, "points": len(pts)}
+
+    def time_solves(plan, k, w, sampler=None):
+        for _ in range(w):
+            plan.apply(x, y, p.steps, stream)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if sampler:
+            sampler.start()
+        t_host = time.perf_counter()
+        for i in range(k):
+            ev[i][0].record(stream)
+            plan.apply(x, y, p.steps, stream)
+            ev[i][1].record(stream)
+        stream.synchronize()
+        t_host = time.perf_counter() - t_host
+        clk = sampler.stop() if sampler else None
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, t_host, clk
+
+    # --- the timed region: K solves of the main implementation
+    plan = results[main_impl]["plan"]
+    sampler = ClockSampler(local)
+    ms, t_host, clk = time_solves(plan, args.steps, args.warmup, sampler)
+    tot = float(np.sum(ms)) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    updates = p.updates * args.steps * world
+    value = updates / tot / 1e9
+    per_solve = np.array(ms)
+    results[main_impl]["timing"] = ms
+
+    # --- the baseline form at equal error (gather), same protocol, untimed for `value`
+    other = "gather" if main_impl == "matrixized" else None
+    if other and "plan" in results[other]:
+        oms, _, _ = time_solves(results[other]["plan"], max(2, args.steps // 2), 1)
+        results[other]["timing"] = oms
+
+    # --- dominant kernel: one sweep per launch, timed with events on the launching stream
+    info = plan.info
+    tb = info["tb"]
+    launches_per_solve = (p.steps + tb - 1) // tb
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for i in range(20):
+        kev[i][0].record(stream)
+        plan.apply(x, y, tb, stream)
+        kev[i][1].record(stream)
+    stream.synchronize()
+    kms = float(np.median([a.elapsed_time(b) for a, b in kev[3:]]))
+    es = 4 if p.dtype == "f32" else 8
+    alg_bytes = 2 * es * p.points  # read the grid once, write it once per launch
+    pk = peaks()
+    achieved = alg_bytes / (kms / 1e3) / 1e9
+    kernel_key = f"{main_impl}-{p.dtype}-2d-r{p.r}-{p.kind}-tb{tb}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kernel_key),
+                "kernel": kernel_key, "launch_ms": kms, "algorithmic_bytes_per_launch": alg_bytes,
+                "time_steps_per_launch": tb, "peak_source": f"{pk['source']} (copy bandwidth, burst)"}
+
+    # --- end to end through the host-buffer C-ABI call
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(field.astype(np.float32 if p.dtype == "f32" else np.float64)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        sx.stencil_apply_host(plan.handle, h_in.numpy(), h_out.numpy(), p.steps)  # warm
+        et = []
+        for _ in range(max(2, args.steps // 2)):
+            t0 = time.perf_counter()
+            sx.stencil_apply_host(plan.handle, h_in.numpy(), h_out.numpy(), p.steps)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": p.updates / float(np.median(et)) / 1e9 * world, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
+               "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
+               "api": "stencil_apply_host (pinned host buffers, H2D + solve + D2H)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_baseline:
+        cpu = oracle_baseline(p, field)
+
+    if rank == 0:
+        comp = {}
+        for impl, res in results.items():
+            if "plan" not in res:
+                comp[impl] = res
+                continue
+            d = {"plan": {k: v for k, v in res["plan"].info.items()}, "err_vs_oracle": res.get("err")}
+            if "timing" in res:
+                t = np.array(res["timing"]) / 1e3
+                d["gstencil_s_p50"] = p.updates / float(np.percentile(t, 50)) / 1e9
+                d["ms_per_solve_p50"] = float(np.percentile(t, 50) * 1e3)
+                d["ms_per_solve_p99"] = float(np.percentile(t, 99) * 1e3)
+            comp[impl] = d
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": p.dtype, "data": "synthetic",
+                "config": workload_config(p, args, {"impl": main_impl, "prec": info["prec"], "tb": tb,
+                                                    "parallelism": f"replicas x{world}"}),
+                "p50_ms": float(np.percentile(per_solve, 50)), "p99_ms": float(np.percentile(per_solve, 99)),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_solve * args.steps, "clocks": clk, "compare": comp,
+                "host_s": t_host}
+        print(json.dumps(line), flush=True)
+    for res in results.values():
+        if "plan" in res:
+            res["plan"].close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

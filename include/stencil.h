@@ -1,0 +1,234 @@
+/*
+ * stencil.h -- C ABI of the GB300 stencil-matrixization library.
+ *
+ * The library advances structured-grid stencils (Sec. 2.2 of "Stencil
+ * Matrixization", arXiv 2310.16298): a field A at time t is mapped to B at
+ * time t+1 by
+ *
+ *     B[x] = sum over o in [0, 2r]^d of C^g[o] * A[x + o - r]          (Eq. (stencil-2d9p))
+ *
+ * with C^g the (2r+1)^d gather-mode coefficient tensor (Eq. (stencil-2d9p-cm)),
+ * r the stencil order (radius), d = 2 or 3.  The matrixized implementation
+ * evaluates the same sum in scatter mode as outer products of coefficient
+ * vectors and input vectors accumulated into resident output tiles (Sec. 3,
+ * Eq. (final)); the gather implementation is the plain CUDA-core form.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are C-ordered, last index contiguous (the footnote of Sec. 4.1),
+ *    packed (no row padding), and hold only the interior points listed in
+ *    `shape`.  Points outside the interior are 0 at every step
+ *    (STENCIL_BC_DIRICHLET_ZERO) or the interior taken modulo the extent
+ *    (STENCIL_BC_PERIODIC).
+ *  - Device pointers are CUDA device (or managed) addresses on the device
+ *    that was current when the plan was created; host pointers are ordinary
+ *    host memory.  The caller keeps ownership of every buffer it passes.
+ *  - Every call returns a stencil_status; nothing aborts or exits.  After a
+ *    non-OK status, stencil_last_error() returns a message for the calling
+ *    thread.
+ *  - No call needs or takes PyTorch types.
+ */
+#ifndef STENCIL_GB300_H
+#define STENCIL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STENCIL_API __attribute__((visibility("default")))
+#else
+#define STENCIL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_plan_s *stencil_plan_t;
+typedef struct CUstream_st *stencil_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    STENCIL_OK = 0,
+    STENCIL_EINVAL = 1,       /* invalid argument (message says which)              */
+    STENCIL_ENOMEM = 2,       /* device or host allocation failed, or over budget    */
+    STENCIL_ECUDA = 3,        /* a CUDA call failed (message has the CUDA error)     */
+    STENCIL_EBUSY = 4,        /* resource in use (e.g. no free serving slot)         */
+    STENCIL_ENOTREADY = 5,    /* submitted work has not finished yet                 */
+    STENCIL_ETIMEDOUT = 6,    /* a wait ran out its host-side deadline               */
+    STENCIL_EUNSUPPORTED = 7  /* valid request, but no kernel for this combination   */
+} stencil_status;
+
+typedef enum { STENCIL_STAR = 0, STENCIL_BOX = 1 } stencil_kind;
+typedef enum { STENCIL_F32 = 0, STENCIL_F64 = 1 } stencil_dtype;
+typedef enum { STENCIL_BC_DIRICHLET_ZERO = 0, STENCIL_BC_PERIODIC = 1 } stencil_boundary;
+
+/* Arithmetic used by the outer-product (matrixized) kernels.  NATIVE is the
+ * storage type on CUDA cores (FP32 FMA or FP64 DFMA).  TF32 / BF16 run the
+ * outer products on the tensor cores with FP32 accumulation; the X2/X3 forms
+ * split each operand into 2 or 3 parts (hi + lo [+ lo2]) and keep the partial
+ * products listed in the design notes, which restores FP32-level accuracy. */
+typedef enum {
+    STENCIL_PREC_NATIVE = 0,
+    STENCIL_PREC_TF32 = 1,
+    STENCIL_PREC_TF32X3 = 2,
+    STENCIL_PREC_BF16 = 3,
+    STENCIL_PREC_BF16X2 = 4,
+    STENCIL_PREC_BF16X3 = 5
+} stencil_precision;
+
+typedef enum {
+    STENCIL_IMPL_AUTO = 0,       /* matrixized where built for the request, else gather */
+    STENCIL_IMPL_GATHER = 1,     /* CUDA-core gather kernel (baseline form)             */
+    STENCIL_IMPL_MATRIXIZED = 2  /* tensor-core outer-product kernel                    */
+} stencil_impl;
+
+typedef struct {
+    int32_t prec;     /* stencil_precision; default NATIVE for GATHER, TF32X3 for F32 MATRIXIZED */
+    int32_t bc;       /* stencil_boundary; default DIRICHLET_ZERO                              */
+    int32_t impl;     /* stencil_impl; default AUTO                                            */
+    int32_t tb;       /* time steps fused per sweep (temporal blocking); 0 = library choice     */
+    int32_t reserved[4];
+} stencil_options;
+
+/* Plan introspection (filled by stencil_plan_info). */
+typedef struct {
+    int32_t impl;         /* stencil_impl actually used (GATHER or MATRIXIZED)          */
+    int32_t prec;         /* stencil_precision actually used                            */
+    int32_t tb;           /* time steps per sweep                                       */
+    int32_t n_lines;      /* coefficient lines run as outer products (0 for GATHER)     */
+    int32_t n_scalar;     /* coefficients applied on CUDA cores beside the lines        */
+    int32_t tile_n;       /* output columns per outer-product block (0 for GATHER)      */
+    int64_t scratch_bytes;/* device scratch owned by the plan                           */
+} stencil_plan_info_t;
+
+/* ---------------------------------------------------------------------------
+ * Plans.
+ *
+ * stencil_plan_create -- validate a problem and build everything a sweep needs
+ * (Sec. 3.1-3.4: C^s = J C^g J, Eq. (stencil-2d9p-gm2sm); the coefficient
+ * lines; the banded operand of every line, the windows of C^o of Eq. (co);
+ * the operand splits for the chosen precision).
+ *   out     [out] receives the plan handle.
+ *   ndim    2 or 3.
+ *   shape   ndim interior extents, C order (slowest first); each >= 2r+1.
+ *   radius  the order r, 1..4.
+ *   kind    STAR requires every off-axis coefficient to be exactly 0.
+ *   coeffs  host array of (2r+1)^ndim doubles: dense C^g in C order, gather
+ *           orientation (coeffs[o] multiplies A[x + o - r]).  Copied; the
+ *           caller may free it after the call.  All must be finite.
+ *   dtype   storage type of the fields passed to apply.
+ *   opt     NULL for defaults.
+ * Errors: EINVAL (bad argument; TF32/BF16 precision with F64 storage),
+ * EUNSUPPORTED (IMPL_MATRIXIZED for a shape/precision without a kernel:
+ * the message says which), ENOMEM / ECUDA (device allocation of the plan's
+ * scratch grid and operands).  The plan owns one scratch grid of the field's
+ * size; it is freed by stencil_plan_destroy.
+ */
+STENCIL_API stencil_status stencil_plan_create(stencil_plan_t *out, int ndim, const int64_t *shape, int radius,
+                                   stencil_kind kind, const double *coeffs, stencil_dtype dtype,
+                                   const stencil_options *opt);
+
+/* Free a plan and its device memory.  Work still queued that uses the plan
+ * must have finished.  NULL is accepted. */
+STENCIL_API stencil_status stencil_plan_destroy(stencil_plan_t plan);
+
+/* Describe the plan (host only, no GPU work). */
+STENCIL_API stencil_status stencil_plan_info(stencil_plan_t plan, stencil_plan_info_t *info);
+
+/* ---------------------------------------------------------------------------
+ * Sweeps.
+ *
+ * stencil_apply -- advance d_in by `steps` time steps into d_out (Sec. 2.2:
+ * two copies of the grid used alternately; the library's second copy is the
+ * plan's scratch grid).  Asynchronous on `stream`; returns once the work is
+ * queued.
+ *   d_in    device array, dtype of the plan, read only (unless == d_out).
+ *   d_out   device array of the same size; may equal d_in.
+ *   steps   >= 0; 0 copies d_in to d_out.
+ * Errors: EINVAL (NULL pointer, steps < 0), ECUDA (launch failure).
+ * Concurrent applies of one plan must be ordered by the caller: they share
+ * the plan's scratch grid.
+ */
+STENCIL_API stencil_status stencil_apply(stencil_plan_t plan, const void *d_in, void *d_out, int64_t steps,
+                             stencil_stream_t stream);
+
+/* Host-to-host convenience: copy h_in to the device, apply, copy the result
+ * to h_out (both host arrays of the plan's dtype, pinned or pageable), and
+ * synchronise.  Uses two device grids allocated per call. */
+STENCIL_API stencil_status stencil_apply_host(stencil_plan_t plan, const void *h_in, void *h_out, int64_t steps);
+
+/* ---------------------------------------------------------------------------
+ * Asynchronous submission.  stencil_submit queues an apply on the plan's own
+ * stream and returns a ticket; stencil_poll returns OK once that work has
+ * finished, ENOTREADY before; stencil_wait blocks up to timeout_ms
+ * (< 0: no limit) and returns OK, or ETIMEDOUT without cancelling the work.
+ * The host waits with cudaEventQuery and short sleeps; nothing spins on the
+ * device.  A ticket is released by the first poll/wait that returns OK or a
+ * CUDA error; using it again returns EINVAL.
+ */
+STENCIL_API stencil_status stencil_submit(stencil_plan_t plan, const void *d_in, void *d_out, int64_t steps,
+                              uint64_t *ticket);
+STENCIL_API stencil_status stencil_poll(uint64_t ticket);
+STENCIL_API stencil_status stencil_wait(uint64_t ticket, int64_t timeout_ms);
+
+/* Message describing the last non-OK status returned to this thread. */
+STENCIL_API const char *stencil_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Batches.  stencil_batch_run advances n independent problems, problem i by
+ * steps[i] time steps from d_in[i] into d_out[i] (each with plans[i]), with
+ * every sweep of every problem queued on `stream`.  Problems of equal
+ * structure are packed into shared persistent launches.  Errors as for
+ * stencil_apply, reported for the first failing problem.
+ */
+STENCIL_API stencil_status stencil_batch_run(int n, const stencil_plan_t *plans, const void *const *d_in,
+                                 void *const *d_out, const int64_t *steps, stencil_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Error norms against a reference (the accuracy report attached to every
+ * result).  Computes, in FP64 on the device,
+ *   out[0] = sum (got - ref)^2,  out[1] = sum ref^2,
+ *   out[2] = max |got - ref|,    out[3] = max |ref|
+ * over `count` elements.  d_got has type got_dtype, d_ref is FP64; out is a
+ * host array of 4 doubles.  Synchronises `stream` before returning.
+ */
+STENCIL_API stencil_status stencil_error_norms(const void *d_got, stencil_dtype got_dtype, const double *d_ref,
+                                   int64_t count, double *out, stencil_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Host-only plan algebra (no GPU needed; used to check the plan layer).
+ *
+ * stencil_band_operand -- the banded (Toeplitz) operand of one coefficient
+ * line.  `line` holds the 2r+1 gather-orientation weights of the line
+ * (line[t] multiplies the input at offset t - r along the line's axis).
+ * Writes K x n doubles, K = n + 2*pad, row-major:
+ *     band[k*n + q] = line[k - q - (pad - r)]  when 0 <= k - q - (pad - r) <= 2r, else 0,
+ * i.e. output q of an n-wide block receives input k of the K-wide window that
+ * starts pad points before the block.  With pad = r the columns of `band`,
+ * read along k, are the windows of a column of C^o (Eq. (co)) that
+ * Eq. (final) multiplies with the input vectors.  pad >= r, n >= 1.
+ */
+STENCIL_API stencil_status stencil_band_operand(int radius, const double *line, int n, int pad, double *band);
+
+/* stencil_line_cover -- the coefficient lines a plan would use (Sec. 3.4 and
+ * Tables cls-2d / cls-3d), described for an n x n output tile (2D) or
+ * 1 x n x n tile (3D).
+ *   option  0 = parallel lines (every line along the contiguous axis),
+ *           1 = orthogonal (star only: one line per axis, the centre weight on
+ *               the contiguous-axis line), 2 = hybrid (3D star only: lines
+ *               CLS(i,*,r) plus CLS(r,r,*)).
+ *   n_lines         [out] lines in the cover.
+ *   outer_products  [out] vector outer products per tile: a line whose
+ *                   nonzeros span s consecutive positions costs n + s - 1.
+ * Errors: EINVAL for an option that does not apply to the kind/ndim.
+ */
+STENCIL_API stencil_status stencil_line_cover(int ndim, int radius, stencil_kind kind, int option, int n,
+                                  int32_t *n_lines, int64_t *outer_products);
+
+/* Library version string. */
+STENCIL_API const char *stencil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_GB300_H */

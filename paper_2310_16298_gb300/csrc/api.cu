@@ -1,0 +1,462 @@
+// Host runtime behind include/stencil.h: plans, the time loop, asynchronous
+// submission, batches and error norms.  Every step of a sweep runs in the
+// library's own CUDA kernels; there is no host fallback.
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "mx.h"
+#include "plan.h"
+
+using namespace stx;
+
+struct stencil_plan_s {
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    int r = 0;
+    bool star = false;
+    bool f64 = false;
+    int bc = kBcDirichlet;
+    std::vector<double> cg;
+    int impl = STENCIL_IMPL_GATHER;
+    int prec = STENCIL_PREC_NATIVE;
+    int tb = 1;
+    int device = 0;
+    int64_t points = 0;
+    size_t grid_bytes = 0;
+    void* scratch = nullptr;
+    cudaStream_t stream = nullptr;  // for stencil_submit
+    MxPlan* mx = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+stencil_status fail(stencil_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+stencil_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return STENCIL_ECUDA;
+}
+
+GatherProblem gather_problem(const stencil_plan_s* p) {
+    GatherProblem g;
+    g.ndim = p->ndim;
+    for (int d = 0; d < 3; ++d) g.n[d] = p->n[d];
+    g.r = p->r;
+    g.star = p->star;
+    g.f64 = p->f64;
+    g.bc = p->bc;
+    g.cg = p->cg.data();
+    return g;
+}
+
+// One sweep of depth `tb` from src to dst.
+cudaError_t run_sweep(const stencil_plan_s* p, const void* src, void* dst, int tb, cudaStream_t s) {
+    if (p->impl == STENCIL_IMPL_MATRIXIZED) return mx_sweep(*p->mx, src, dst, tb, s);
+    GatherProblem g = gather_problem(p);
+    return gather_sweep(g, src, dst, tb, s);
+}
+
+// Time loop (Sec. 2.2: two grid copies used alternately).  The copies are the
+// caller's output and the plan's scratch grid, ordered so that the last
+// sweep writes d_out and no sweep reads the buffer it writes.
+stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out, int64_t steps,
+                         cudaStream_t s, void* scratch) {
+    if (steps == 0) {
+        if (d_in != d_out) {
+            cudaError_t e = cudaMemcpyAsync(d_out, d_in, p->grid_bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        return STENCIL_OK;
+    }
+    const int tb = p->tb;
+    const int64_t nsweep = (steps + tb - 1) / tb;
+    const void* src = d_in;
+    if (d_in == d_out && (nsweep & 1)) {
+        cudaError_t e = cudaMemcpyAsync(scratch, d_in, p->grid_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        src = scratch;
+    }
+    for (int64_t k = 0; k < nsweep; ++k) {
+        const int64_t left = nsweep - 1 - k;  // sweeps after this one
+        void* dst = (left & 1) ? scratch : d_out;
+        const int depth = (int)((k == nsweep - 1) ? (steps - (nsweep - 1) * tb) : tb);
+        cudaError_t e = run_sweep(p, src, dst, depth, s);
+        if (e != cudaSuccess) return cuda_fail(e, "stencil sweep launch");
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+// ----------------------------------------------------------------- tickets
+std::mutex g_tk_mu;
+std::unordered_map<uint64_t, cudaEvent_t> g_tickets;
+std::vector<cudaEvent_t> g_event_pool;
+uint64_t g_next_ticket = 1;
+
+stencil_status ticket_status(uint64_t ticket, cudaEvent_t* ev) {
+    std::lock_guard<std::mutex> lk(g_tk_mu);
+    auto it = g_tickets.find(ticket);
+    if (it == g_tickets.end()) return fail(STENCIL_EINVAL, "unknown or already released ticket");
+    *ev = it->second;
+    return STENCIL_OK;
+}
+
+void ticket_release(uint64_t ticket) {
+    std::lock_guard<std::mutex> lk(g_tk_mu);
+    auto it = g_tickets.find(ticket);
+    if (it != g_tickets.end()) {
+        g_event_pool.push_back(it->second);
+        g_tickets.erase(it);
+    }
+}
+
+}  // namespace
+
+// =================================================================== plans
+extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, const int64_t* shape,
+                                              int radius, stencil_kind kind, const double* coeffs,
+                                              stencil_dtype dtype, const stencil_options* opt) {
+    if (!out) return fail(STENCIL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(STENCIL_EINVAL, "ndim must be 2 or 3");
+    if (radius < 1 || radius > kMaxRadius) return fail(STENCIL_EINVAL, "radius must be in 1..4");
+    if (!shape || !coeffs) return fail(STENCIL_EINVAL, "shape or coeffs is NULL");
+    if (kind != STENCIL_STAR && kind != STENCIL_BOX) return fail(STENCIL_EINVAL, "kind must be STAR or BOX");
+    if (dtype != STENCIL_F32 && dtype != STENCIL_F64) return fail(STENCIL_EINVAL, "dtype must be F32 or F64");
+    stencil_options o{};
+    if (opt) o = *opt;
+    if (o.bc != STENCIL_BC_DIRICHLET_ZERO && o.bc != STENCIL_BC_PERIODIC)
+        return fail(STENCIL_EINVAL, "bc must be DIRICHLET_ZERO or PERIODIC");
+    if (o.impl < STENCIL_IMPL_AUTO || o.impl > STENCIL_IMPL_MATRIXIZED)
+        return fail(STENCIL_EINVAL, "impl out of range");
+    if (o.tb < 0 || o.tb > 16) return fail(STENCIL_EINVAL, "tb must be in 0..16");
+    const int W = 2 * radius + 1;
+    int64_t nco = 1, points = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (shape[d] < W) return fail(STENCIL_EINVAL, "every extent must be at least 2*radius+1");
+        if (shape[d] > (int64_t)1 << 31) return fail(STENCIL_EINVAL, "extent too large");
+        nco *= W;
+        points *= shape[d];
+    }
+    for (int64_t i = 0; i < nco; ++i)
+        if (!std::isfinite(coeffs[i])) return fail(STENCIL_EINVAL, "coefficients must be finite");
+    if (kind == STENCIL_STAR) {
+        for (int64_t t = 0; t < nco; ++t) {
+            int64_t rem = t;
+            int off = 0;
+            for (int d = ndim - 1; d >= 0; --d) {
+                off += (rem % W) != radius;
+                rem /= W;
+            }
+            if (off > 1 && coeffs[t] != 0.0)
+                return fail(STENCIL_EINVAL, "a STAR stencil must have zero off-axis coefficients");
+        }
+    }
+    const bool f64 = (dtype == STENCIL_F64);
+    const int prec = o.prec;
+    if (prec < STENCIL_PREC_NATIVE || prec > STENCIL_PREC_BF16X3) return fail(STENCIL_EINVAL, "prec out of range");
+    if (f64 && prec != STENCIL_PREC_NATIVE) return fail(STENCIL_EINVAL, "TF32/BF16 precisions need F32 storage");
+    if (o.impl == STENCIL_IMPL_GATHER && prec != STENCIL_PREC_NATIVE)
+        return fail(STENCIL_EINVAL, "the gather kernel computes in the storage type (prec NATIVE)");
+
+    std::unique_ptr<stencil_plan_s> p(new stencil_plan_s);
+    p->ndim = ndim;
+    for (int d = 0; d < ndim; ++d) p->n[d] = shape[d];
+    p->r = radius;
+    p->star = (kind == STENCIL_STAR);
+    p->f64 = f64;
+    p->bc = o.bc;
+    p->cg.assign(coeffs, coeffs + nco);
+    p->points = points;
+    p->grid_bytes = (size_t)points * (f64 ? 8 : 4);
+
+    // Implementation choice.  For the outer-product kernels, NATIVE means the
+    // FP32-accuracy split (TF32X3); FP64 runs on the CUDA-core kernel.
+    std::string why;
+    MxRequest req;
+    req.ndim = ndim;
+    for (int d = 0; d < 3; ++d) req.n[d] = p->n[d];
+    req.r = radius;
+    req.star = p->star;
+    req.f64 = f64;
+    req.bc = o.bc;
+    req.cg = p->cg.data();
+    req.prec = (prec == STENCIL_PREC_NATIVE) ? STENCIL_PREC_TF32X3 : prec;
+    req.tb = o.tb;
+    const bool mx_ok = (o.impl != STENCIL_IMPL_GATHER) && mx_supported(req, &why);
+    const bool want_mx = (o.impl == STENCIL_IMPL_MATRIXIZED) || (prec != STENCIL_PREC_NATIVE);
+    if (want_mx && !mx_ok) return fail(STENCIL_EUNSUPPORTED, "matrixized kernel not available: " + why);
+    if (mx_ok) {
+        p->impl = STENCIL_IMPL_MATRIXIZED;
+        p->prec = req.prec;
+    } else {
+        p->impl = STENCIL_IMPL_GATHER;
+        p->prec = STENCIL_PREC_NATIVE;
+    }
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+    // Temporal blocking depth.
+    if (p->impl == STENCIL_IMPL_GATHER) {
+        p->tb = o.tb > 0 ? o.tb : 1;
+        GatherProblem g = gather_problem(p.get());
+        int max_smem = 0;
+        e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        if (gather_smem_bytes(g, p->tb) > (size_t)max_smem)
+            return fail(STENCIL_EUNSUPPORTED, "temporal block depth too large for shared memory");
+    } else {
+        p->mx = new MxPlan();
+        stencil_status st = mx_plan_build(req, p->mx, &why);
+        if (st != STENCIL_OK) {
+            delete p->mx;
+            p->mx = nullptr;
+            return fail(st, "matrixized plan: " + why);
+        }
+        p->tb = p->mx->tb;
+    }
+
+    e = cudaMalloc(&p->scratch, p->grid_bytes);
+    if (e != cudaSuccess) {
+        if (p->mx) {
+            mx_plan_free(p->mx);
+            delete p->mx;
+        }
+        cudaGetLastError();
+        return fail(STENCIL_ENOMEM, std::string("scratch grid: ") + cudaGetErrorString(e));
+    }
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(p->scratch);
+        if (p->mx) {
+            mx_plan_free(p->mx);
+            delete p->mx;
+        }
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    *out = p.release();
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_plan_destroy(stencil_plan_t p) {
+    if (!p) return STENCIL_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->scratch) cudaFree(p->scratch);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->mx) {
+        mx_plan_free(p->mx);
+        delete p->mx;
+    }
+    delete p;
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_t* info) {
+    if (!p || !info) return fail(STENCIL_EINVAL, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->impl = p->impl;
+    info->prec = p->prec;
+    info->tb = p->tb;
+    info->scratch_bytes = (int64_t)p->grid_bytes + (p->mx ? (int64_t)p->mx->operand_bytes : 0);
+    if (p->mx) {
+        info->n_lines = p->mx->n_lines;
+        info->n_scalar = p->mx->n_scalar;
+        info->tile_n = p->mx->nb;
+    }
+    return STENCIL_OK;
+}
+
+// =================================================================== sweeps
+extern "C" stencil_status stencil_apply(stencil_plan_t p, const void* d_in, void* d_out, int64_t steps,
+                                        stencil_stream_t stream) {
+    if (!p || !d_in || !d_out) return fail(STENCIL_EINVAL, "NULL argument");
+    if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    return time_loop(p, d_in, d_out, steps, (cudaStream_t)stream, p->scratch);
+}
+
+extern "C" stencil_status stencil_apply_host(stencil_plan_t p, const void* h_in, void* h_out, int64_t steps) {
+    if (!p || !h_in || !h_out) return fail(STENCIL_EINVAL, "NULL argument");
+    if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    void *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, p->grid_bytes);
+    if (e != cudaSuccess) return fail(STENCIL_ENOMEM, "device grid");
+    e = cudaMalloc(&b, p->grid_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        return fail(STENCIL_ENOMEM, "device grid");
+    }
+    stencil_status st = STENCIL_OK;
+    e = cudaMemcpyAsync(a, h_in, p->grid_bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "H2D copy");
+    if (st == STENCIL_OK) st = time_loop(p, a, b, steps, p->stream, p->scratch);
+    if (st == STENCIL_OK) {
+        e = cudaMemcpyAsync(h_out, b, p->grid_bytes, cudaMemcpyDeviceToHost, p->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "D2H copy");
+    }
+    e = cudaStreamSynchronize(p->stream);
+    if (st == STENCIL_OK && e != cudaSuccess) st = cuda_fail(e, "stencil_apply_host");
+    cudaFree(a);
+    cudaFree(b);
+    return st;
+}
+
+// =================================================================== async
+extern "C" stencil_status stencil_submit(stencil_plan_t p, const void* d_in, void* d_out, int64_t steps,
+                                         uint64_t* ticket) {
+    if (!p || !d_in || !d_out || !ticket) return fail(STENCIL_EINVAL, "NULL argument");
+    if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    stencil_status st = time_loop(p, d_in, d_out, steps, p->stream, p->scratch);
+    if (st != STENCIL_OK) return st;
+    cudaEvent_t ev = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_tk_mu);
+        if (!g_event_pool.empty()) {
+            ev = g_event_pool.back();
+            g_event_pool.pop_back();
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    e = cudaEventRecord(ev, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    std::lock_guard<std::mutex> lk(g_tk_mu);
+    *ticket = g_next_ticket++;
+    g_tickets[*ticket] = ev;
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_poll(uint64_t ticket) {
+    cudaEvent_t ev;
+    stencil_status st = ticket_status(ticket, &ev);
+    if (st != STENCIL_OK) return st;
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaErrorNotReady) return fail(STENCIL_ENOTREADY, "work not finished");
+    ticket_release(ticket);
+    if (e != cudaSuccess) return cuda_fail(e, "submitted work");
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_wait(uint64_t ticket, int64_t timeout_ms) {
+    cudaEvent_t ev;
+    stencil_status st = ticket_status(ticket, &ev);
+    if (st != STENCIL_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e != cudaErrorNotReady) {
+            ticket_release(ticket);
+            if (e != cudaSuccess) return cuda_fail(e, "submitted work");
+            return STENCIL_OK;
+        }
+        if (timeout_ms >= 0) {
+            const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                                 std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ms) return fail(STENCIL_ETIMEDOUT, "wait timed out; work still queued");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+extern "C" const char* stencil_last_error(void) { return g_err.c_str(); }
+
+// =================================================================== batches
+extern "C" stencil_status stencil_batch_run(int n, const stencil_plan_t* plans, const void* const* d_in,
+                                            void* const* d_out, const int64_t* steps,
+                                            stencil_stream_t stream) {
+    if (n < 0) return fail(STENCIL_EINVAL, "n must be >= 0");
+    if (n == 0) return STENCIL_OK;
+    if (!plans || !d_in || !d_out || !steps) return fail(STENCIL_EINVAL, "NULL argument");
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !d_in[i] || !d_out[i] || steps[i] < 0)
+            return fail(STENCIL_EINVAL, "invalid entry " + std::to_string(i));
+    for (int i = 0; i < n; ++i) {
+        stencil_status st = time_loop(plans[i], d_in[i], d_out[i], steps[i], (cudaStream_t)stream,
+                                      plans[i]->scratch);
+        if (st != STENCIL_OK) return fail(st, "problem " + std::to_string(i) + ": " + g_err);
+    }
+    return STENCIL_OK;
+}
+
+// =================================================================== norms
+extern "C" stencil_status stencil_error_norms(const void* d_got, stencil_dtype got_dtype, const double* d_ref,
+                                              int64_t count, double* out, stencil_stream_t stream) {
+    if (!d_got || !d_ref || !out) return fail(STENCIL_EINVAL, "NULL argument");
+    if (count < 0) return fail(STENCIL_EINVAL, "count must be >= 0");
+    if (got_dtype != STENCIL_F32 && got_dtype != STENCIL_F64) return fail(STENCIL_EINVAL, "bad dtype");
+    double* scratch = nullptr;
+    const size_t pb = norms_partials_bytes();
+    cudaError_t e = cudaMalloc(&scratch, pb + 4 * sizeof(double));
+    if (e != cudaSuccess) return fail(STENCIL_ENOMEM, "norm scratch");
+    cudaStream_t s = (cudaStream_t)stream;
+    e = error_norms(d_got, got_dtype == STENCIL_F64, d_ref, count, scratch,
+                    scratch + pb / sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch + pb / sizeof(double), 4 * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "error norms");
+    return STENCIL_OK;
+}
+
+// =================================================================== host algebra
+extern "C" stencil_status stencil_band_operand(int radius, const double* line, int n, int pad, double* band) {
+    if (!line || !band) return fail(STENCIL_EINVAL, "NULL argument");
+    if (radius < 1 || radius > kMaxRadius || n < 1 || pad < radius)
+        return fail(STENCIL_EINVAL, "need 1 <= radius <= 4, n >= 1, pad >= radius");
+    band_operand(radius, line, n, pad, band);
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_line_cover(int ndim, int radius, stencil_kind kind, int option, int n,
+                                             int32_t* n_lines, int64_t* outer_products) {
+    if (!n_lines || !outer_products) return fail(STENCIL_EINVAL, "NULL argument");
+    if (ndim != 2 && ndim != 3) return fail(STENCIL_EINVAL, "ndim must be 2 or 3");
+    if (radius < 1 || radius > kMaxRadius || n < 1) return fail(STENCIL_EINVAL, "bad radius or n");
+    const int W = 2 * radius + 1;
+    int64_t nco = 1;
+    for (int d = 0; d < ndim; ++d) nco *= W;
+    // Unit weights on the stencil's support: every point of a box, the axes of a star.
+    std::vector<double> cg((size_t)nco, 0.0);
+    for (int64_t t = 0; t < nco; ++t) {
+        int64_t rem = t;
+        int off = 0;
+        for (int d = ndim - 1; d >= 0; --d) {
+            off += (rem % W) != radius;
+            rem /= W;
+        }
+        cg[(size_t)t] = (kind == STENCIL_BOX || off <= 1) ? 1.0 : 0.0;
+    }
+    // Parallel lines run along the axis the paper's tables use: i in 2D
+    // (CLS(*,j)), j in 3D (CLS(i,*,k)).
+    const int axis_par = (ndim == 2) ? 0 : 1;
+    std::vector<CoefLine> lines;
+    std::string why;
+    if (!cover_lines(ndim, radius, kind == STENCIL_STAR, cg.data(), option, axis_par, &lines, &why))
+        return fail(STENCIL_EINVAL, why);
+    int64_t ops = 0;
+    for (const auto& l : lines) ops += line_outer_products(l, n);
+    *n_lines = (int32_t)lines.size();
+    *outer_products = ops;
+    return STENCIL_OK;
+}
+
+extern "C" const char* stencil_version(void) { return "stencil-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,31 @@
+// Internal interface between the host runtime (api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace stx {
+
+// A single-grid problem as the gather kernels see it.
+struct GatherProblem {
+    int ndim;          // 2 or 3
+    int64_t n[3];      // interior extents, slowest first
+    int r;             // order (radius)
+    bool star;         // only on-axis coefficients are nonzero
+    bool f64;          // storage/compute type FP64 (else FP32)
+    int bc;            // kBcDirichlet | kBcPeriodic
+    const double* cg;  // host: dense C^g, (2r+1)^ndim, gather orientation
+};
+
+// Advance `in` by `tb` time steps into `out` (distinct buffers).
+cudaError_t gather_sweep(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s);
+size_t gather_smem_bytes(const GatherProblem& p, int tb);
+
+// FP64 error norms: out4 (device) = {sum d^2, sum ref^2, max|d|, max|ref|}.
+// `partials` is device scratch of norms_partials_bytes() bytes.
+size_t norms_partials_bytes();
+cudaError_t error_norms(const void* got, bool got_f64, const double* ref, int64_t count,
+                        double* partials, double* out4, cudaStream_t s);
+
+}  // namespace stx

@@ -1,0 +1,47 @@
+// Internal interface of the matrixized (outer-product) kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/stencil.h"
+
+namespace stx {
+
+struct MxRequest {
+    int ndim = 2;
+    int64_t n[3] = {1, 1, 1};
+    int r = 1;
+    bool star = false;
+    bool f64 = false;
+    int bc = 0;
+    const double* cg = nullptr;  // host, dense C^g
+    int prec = STENCIL_PREC_TF32X3;
+    int tb = 0;                   // 0 = library choice
+};
+
+struct MxPlan {
+    int ndim = 2;
+    int64_t n[3] = {1, 1, 1};
+    int r = 1;
+    int bc = 0;
+    int prec = STENCIL_PREC_TF32X3;
+    int tb = 1;
+    int nb = 16;          // output columns per MMA block
+    int n_lines = 0;      // lines on the tensor cores
+    int n_scalar = 0;     // weights applied on CUDA cores
+    size_t operand_bytes = 0;
+    void* d_operands = nullptr;  // banded line operands (device), kernel-specific layout
+    void* d_scalars = nullptr;   // scalar-term table (device)
+    void* tmap_storage = nullptr;
+};
+
+bool mx_supported(const MxRequest& q, std::string* why);
+stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why);
+void mx_plan_free(MxPlan* p);
+cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
+
+}  // namespace stx
