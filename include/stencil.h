@@ -98,6 +98,8 @@ typedef struct {
     int32_t n_scalar;     /* coefficients applied on CUDA cores beside the lines        */
     int32_t tile_n;       /* output columns per outer-product block (0 for GATHER)      */
     int64_t scratch_bytes;/* device scratch owned by the plan                           */
+    int32_t device_error; /* nonzero once a kernel of the plan gave up a bounded wait     */
+    int32_t reserved;
 } stencil_plan_info_t;
 
 /* ---------------------------------------------------------------------------

@@ -280,6 +280,7 @@ extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_
         info->n_lines = p->mx->n_lines;
         info->n_scalar = p->mx->n_scalar;
         info->tile_n = p->mx->nb;
+        info->device_error = (int32_t)mx_device_error(*p->mx);
     }
     return STENCIL_OK;
 }

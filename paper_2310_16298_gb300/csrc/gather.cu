@@ -17,27 +17,41 @@ namespace {
 constexpr int kBX = 32;   // threads along the contiguous axis (one warp)
 constexpr int kRS = 8;    // outputs per thread along the strip axis
 
+// Asynchronous global->shared copy of one element (Ampere-style cp.async):
+// many copies stay in flight per thread, so the tile load runs at HBM rate.
 template <typename T>
-__device__ __forceinline__ T fetch2(const T* __restrict__ a, int64_t y, int64_t x, int64_t ny,
-                                    int64_t nx, int bc) {
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Address of a tile element after the boundary rule, or nullptr for a zero.
+template <typename T>
+__device__ __forceinline__ const T* src2(const T* __restrict__ a, int64_t y, int64_t x, int64_t ny,
+                                         int64_t nx, int bc) {
     if (y < 0 || y >= ny || x < 0 || x >= nx) {
-        if (bc == kBcDirichlet) return T(0);
+        if (bc == kBcDirichlet) return nullptr;
         y = wrap_index(y, ny);
         x = wrap_index(x, nx);
     }
-    return a[y * nx + x];
+    return a + y * nx + x;
 }
 
 template <typename T>
-__device__ __forceinline__ T fetch3(const T* __restrict__ a, int64_t z, int64_t y, int64_t x,
-                                    int64_t nz, int64_t ny, int64_t nx, int bc) {
+__device__ __forceinline__ const T* src3(const T* __restrict__ a, int64_t z, int64_t y, int64_t x,
+                                         int64_t nz, int64_t ny, int64_t nx, int bc) {
     if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) {
-        if (bc == kBcDirichlet) return T(0);
+        if (bc == kBcDirichlet) return nullptr;
         z = wrap_index(z, nz);
         y = wrap_index(y, ny);
         x = wrap_index(x, nx);
     }
-    return a[(z * ny + y) * nx + x];
+    return a + (z * ny + y) * nx + x;
 }
 
 // ---------------------------------------------------------------------------
@@ -64,11 +78,14 @@ gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64
         const int64_t gy = y0 - H + sy;
         for (int sx = tx; sx < SX; sx += kBX) {
             const int64_t gx = x0 - H + sx;
-            T v = T(0);
-            if (sy < SY) v = interior ? in[gy * nx + gx] : fetch2(in, gy, gx, ny, nx, bc);
-            smem[sy * SX + sx] = v;
+            T* d = smem + sy * SX + sx;
+            const T* g = nullptr;
+            if (sy < SY) g = interior ? in + gy * nx + gx : src2(in, gy, gx, ny, nx, bc);
+            if (g) cp_async_elem(d, g);
+            else *d = T(0);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     for (int t = 1; t <= tb; ++t) {
@@ -150,13 +167,15 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
             const int64_t gy = y0 - H + sy;
             for (int sx = tx; sx < SX; sx += kBX) {
                 const int64_t gx = x0 - H + sx;
-                T v = T(0);
-                if (sz < SZ)
-                    v = interior ? in[(gz * ny + gy) * nx + gx] : fetch3(in, gz, gy, gx, nz, ny, nx, bc);
-                smem[sz * plane + sy * SX + sx] = v;
+                T* d = smem + sz * plane + sy * SX + sx;
+                const T* g = nullptr;
+                if (sz < SZ) g = interior ? in + (gz * ny + gy) * nx + gx : src3(in, gz, gy, gx, nz, ny, nx, bc);
+                if (g) cp_async_elem(d, g);
+                else *d = T(0);
             }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     for (int t = 1; t <= tb; ++t) {
@@ -221,7 +240,7 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
 }
 
 // Tile shapes.
-constexpr int k2BY = 8, k2TX = 128, k2TY = 32;
+constexpr int k2BY = 8, k2TX = 128, k2TY = 64;
 constexpr int k3BY = 8, k3TX = 32, k3TY = 16, k3TZ = 8;
 
 template <typename T>

@@ -43,5 +43,8 @@ bool mx_supported(const MxRequest& q, std::string* why);
 stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why);
 void mx_plan_free(MxPlan* p);
 cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
+// Nonzero when a kernel of this plan gave up a bounded wait (bit 0: operand
+// staging, bit 1: tensor-core completion).
+unsigned int mx_device_error(const MxPlan& p);
 
 }  // namespace stx

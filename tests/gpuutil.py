@@ -29,7 +29,7 @@ def run(field: np.ndarray, r: int, kind: str, cg: np.ndarray, dtype: str, bc: st
     buf_in = torch.full((n + 2 * GUARD,), CANARY, dtype=td, device="cuda")
     buf_out = torch.full((n + 2 * GUARD,), CANARY, dtype=td, device="cuda")
     x = buf_in[GUARD:GUARD + n]
-    x.copy_(torch.from_numpy(np.ascontiguousarray(field)).to(td))
+    x.copy_(torch.from_numpy(np.ascontiguousarray(field).ravel()).to(td))
     y = x if alias else buf_out[GUARD:GUARD + n]
     plan = sx.stencil_plan_create(field.shape, r, kind, cg, dtype, sx.make_options(prec, bc, impl, tb))
     try:
@@ -45,7 +45,7 @@ def run(field: np.ndarray, r: int, kind: str, cg: np.ndarray, dtype: str, bc: st
             tail = buf[GUARD + n:].double().cpu().numpy()
             assert np.all(head == CANARY) and np.all(tail == CANARY), "guard band overwritten"
         if not alias:
-            assert np.array_equal(buf_in[GUARD:GUARD + n].cpu().numpy(),
+            assert np.array_equal(buf_in[GUARD:GUARD + n].cpu().numpy().reshape(field.shape),
                                   np.ascontiguousarray(field).astype(np.float32 if dtype == "f32" else np.float64)), \
                 "input grid modified"
     return y.double().cpu().numpy().reshape(field.shape), info

@@ -1,0 +1,84 @@
+"""GPU parity of the matrixized (tcgen05 outer-product) kernel against the
+FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+from gpuutil import TOL, check, run
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(ndim, shape, r, kind, seed, lo=-1.0, hi=1.0):
+    cg = si.coeffs_random(ndim, r, kind, 200 + seed, dtype="f32")
+    a = si.round_to(si.field_uniform(shape, seed, lo, hi), "f32")
+    return a, cg
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("kind", ["box", "star"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_mx_2d(prec, bc, kind, r):
+    shape = (300 + r, 196 + 4 * r)  # several tiles in both axes plus ragged tails
+    a, cg = problem(2, shape, r, kind, seed=r)
+    steps = 3
+    got, info = run(a, r, kind, cg, "f32", bc, steps, impl="matrixized", prec=prec)
+    assert info["impl"] == 2 and info["device_error"] == 0
+    check(got, oracle.gather(a, r, cg, bc, steps), TOL[prec], f"mx 2d r={r} {kind} {bc} {prec}")
+
+
+@pytest.mark.parametrize("shape", [(5, 8), (37, 20), (129, 68), (128, 64), (256, 128), (130, 4 * 33)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_mx_2d_shapes(shape, bc):
+    r = 2
+    if min(shape) < 2 * r + 1:
+        pytest.skip("below the minimum extent")
+    a, cg = problem(2, shape, r, "box", seed=sum(shape))
+    got, info = run(a, r, "box", cg, "f32", bc, 4, impl="matrixized", prec="tf32x3")
+    assert info["device_error"] == 0
+    check(got, oracle.gather(a, r, cg, bc, 4), 1e-5, f"mx shape {shape} {bc}")
+
+
+def test_mx_exact_when_operands_are_tf32():
+    """Inputs and weights exactly representable in TF32 (small dyadic values):
+    the lo parts vanish and TF32x3 matches the FP32 CUDA-core result to 1e-6."""
+    rng = np.random.default_rng(1)
+    shape = (160, 96)
+    a = rng.integers(-64, 65, size=shape) / 64.0
+    cg = rng.integers(-8, 9, size=(5, 5)) / 64.0
+    mx, _ = run(a, 2, "box", cg, "f32", "periodic", 2, impl="matrixized", prec="tf32x3")
+    ga, _ = run(a, 2, "box", cg, "f32", "periodic", 2, impl="gather")
+    want = oracle.gather(a, 2, cg, "periodic", 2)
+    check(mx, want, 1e-6, "mx exact operands")
+    check(ga, want, 1e-6, "gather exact operands")
+
+
+def test_mx_auto_picks_matrixized_for_f32_box():
+    a, cg = problem(2, (64, 64), 1, "box", seed=9)
+    _, info = run(a, 1, "box", cg, "f32", "dirichlet", 1, impl="auto")
+    assert info["impl"] == 2 and info["prec"] == 2
+
+
+def test_mx_split_runs_bitwise():
+    a, cg = problem(2, (200, 136), 2, "box", seed=11)
+    full, _ = run(a, 2, "box", cg, "f32", "periodic", 6, impl="matrixized")
+    part, _ = run(a, 2, "box", cg, "f32", "periodic", 2, impl="matrixized")
+    rest, _ = run(part, 2, "box", cg, "f32", "periodic", 4, impl="matrixized")
+    assert np.array_equal(full, rest)
+
+
+def test_mx_in_place_and_zero_steps():
+    a, cg = problem(2, (140, 72), 1, "box", seed=12)
+    got, _ = run(a, 1, "box", cg, "f32", "dirichlet", 3, impl="matrixized", alias=True, check_guard=False)
+    check(got, oracle.gather(a, 1, cg, "dirichlet", 3), 1e-5)
+    got, _ = run(a, 1, "box", cg, "f32", "dirichlet", 0, impl="matrixized")
+    assert np.array_equal(got, a)
+
+
+def test_mx_rejects_unaligned_rows():
+    import paper_2310_16298_gb300 as sx
+    with pytest.raises(sx.StencilError) as ei:
+        sx.stencil_plan_create((64, 66), 1, "box", np.ones((3, 3)) / 9, "f32", sx.make_options(impl="matrixized"))
+    assert ei.value.status == sx.EUNSUPPORTED
