@@ -44,37 +44,33 @@ namespace stx {
 
 namespace {
 
-constexpr int kNb = 16;                 // output columns per line per MMA block
 constexpr int kPad = 4;                 // input columns left/right of the output columns
-constexpr int kK = kNb + 2 * kPad;      // K window per block (24)
-constexpr int kKSteps = kK / 8;         // tf32 MMAs (K = 8) per window (3)
-constexpr int kKChunks = kK / 4;        // 16-byte K chunks per window (6)
 constexpr int kSlabRows = 32;           // input rows per warp slab (= TMEM lanes of one warp)
-constexpr int kMathWarps = 4;           // one per TMEM lane quarter
+constexpr int kQuarters = 4;            // TMEM lane quarters = warp slabs per tile
+constexpr int kMathWarps = 8;           // two per lane quarter, each taking half of the columns
 constexpr int kThreads = 64 + 32 * kMathWarps;  // producer warp, MMA warp, math warps
 constexpr int kMathThreads = 32 * kMathWarps;
-constexpr int kMaxLines = 2 * kMaxRadius + 1;
-constexpr int kMaxBlocks = 2;
-constexpr int kMaxInW = kMaxBlocks * kNb + 2 * kPad;  // 40
 constexpr int kRawStages = 6;           // TMA ring depth
 constexpr int kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
+// Output columns per tile (the MMA block width) for a stencil with L lines:
+// 32 while both accumulator sets (2 x L x 32 columns) and both A stages
+// (2 x 2 x 40 columns) fit the 512 TMEM columns, else 16.
+__host__ __device__ constexpr int tile_nb(int L) { return (2 * L * 32 + 4 * (32 + 2 * kPad) <= kTmemCols) ? 32 : 16; }
+
 struct MxArgs2D {
     float* out;
     const float* in;          // source grid (periodic halo fix-up reads it directly)
-    const float* bops;        // banded operands [part][kchunk][line*16 + q][4]
+    const float* bops;        // banded operands [part][kchunk][line*NB + q][4]
     unsigned int* err;        // device error word (host-mapped)
     int ny, nx;
-    int r, bc, nlines, nprod;  // nprod: 1 (TF32) or 3 (TF32x3)
-    int nblk;                  // MMA blocks (of kNb output columns) per tile
-    int in_w;                  // input columns per tile: nblk*16 + 8
-    int rows_out;              // output rows per warp slab: 32 - 2r
+    int bc, nprod;             // nprod: 1 (TF32) or 3 (TF32x3)
     int tiles_x, tiles_total;
     uint32_t bop_bytes;        // both parts
 };
 
-__host__ __device__ inline int raw_stage_bytes(int in_w) { return kMathWarps * kSlabRows * in_w * 4; }
+__host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
 
 size_t smem_bytes_2d(int in_w, uint32_t bop_bytes) {
     return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + bop_bytes +
@@ -94,35 +90,52 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
     return true;
 }
 
-// Persistent, warp-specialised sweep.
+// TF32 high part by integer rounding (nearest, ties away from zero): the low
+// 13 mantissa bits are cleared after adding half of their weight.
+__device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+
+// Persistent, warp-specialised sweep (R = order; NB = output columns per tile).
 //  * Warp 0 streams input tiles with TMA into a ring of shared-memory buffers.
 //    A tile is four overlapping 32-row slabs (one per TMEM lane quarter) of
-//    nblk*16 + 8 columns; slab q covers input rows Y0 + q*(32-2r) - r + [0, 32).
-//  * Warps 2..5 (one per lane quarter) split their slab into TF32 hi and lo
-//    parts and write them straight into tensor memory (tcgen05.st): the
-//    A operand never goes back through shared memory.  One tile behind, the
+//    NB + 8 columns; slab q covers input rows Y0 + q*(32-2R) - R + [0, 32).
+//  * Warps 2..9 (two per lane quarter) split their slab into TF32 hi and lo
+//    parts and write them straight into tensor memory (tcgen05.st): the A
+//    operand never goes back through shared memory.  One tile behind, the
 //    same warps drain the accumulators and write the outputs.
-//  * Warp 1 issues the outer products.  All coefficient lines of the stencil
-//    sit side by side along N (B = [H_0 | H_1 | ... ], N = 16 * lines), so one
-//    tcgen05.mma applies every line to the same input rows; line a's partial
-//    sums land in columns a*16 .. a*16+15.  The row shift a - r of each line
-//    is applied in the epilogue with warp shuffles, which is why each warp
-//    slab yields 32 - 2r output rows.
+//  * Warp 1 issues the outer products.  All 2R+1 coefficient lines of the
+//    stencil sit side by side along N (B = [H_0 | ... | H_2R], N = NB (2R+1)),
+//    so one tcgen05.mma applies every line to the same input rows; line a's
+//    partial sums land in columns a*NB .. a*NB+NB-1.  The row shift a - R of
+//    each line is applied in the epilogue with warp shuffles, which is why
+//    each 32-row warp slab yields 32 - 2R output rows.
 //  * Accuracy: TF32x3 products are accumulated corrections first (lo*hi,
 //    hi*lo) and the large hi*hi products last, so each line accumulator sees
-//    only kKSteps large additions (the tensor core's FP32 accumulation
-//    truncates); lines are summed in FP32 round-to-nearest in the epilogue.
+//    only (NB+8)/8 large additions (the tensor core's FP32 accumulation
+//    truncates); the lines are summed in FP32 round-to-nearest in the
+//    epilogue.
+template <int R, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
 mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
+    constexpr int L = 2 * R + 1;            // lines
+    constexpr int N = L * NB;               // MMA N
+    constexpr int K = NB + 2 * kPad;        // input columns per tile = K window
+    constexpr int KS = K / 8;               // tf32 MMAs per window
+    constexpr int ROWS_OUT = kSlabRows - 2 * R;
+    constexpr int A_COLS = 2 * K;           // TMEM columns of one A stage (hi | lo)
+    constexpr int HALF = NB / 2;            // epilogue columns per math warp
+    constexpr int RSB = raw_stage_bytes(K);
+    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
+    static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
+
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int in_w = args.in_w;
-    const int RSB = raw_stage_bytes(in_w);
     unsigned char* raw = smem;                                // kRawStages tiles
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;                          // [kRawStages] TMA landed
-    uint64_t* rawfree = bars + kRawStages;          // [kRawStages] slab read by its math warp
+    uint64_t* rawfree = bars + kRawStages;          // [kRawStages] slab read by its math warps
     uint64_t* afull = bars + 2 * kRawStages;        // [2] A operand stage written to TMEM
     uint64_t* aempty = afull + 2;                   // [2] MMAs done reading the A stage
     uint64_t* accf = aempty + 2;                    // [2] accumulator set ready
@@ -133,12 +146,6 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int r = args.r;
-    const int L = args.nlines;
-    const int N = L * kNb;                 // MMA N: all lines side by side
-    const int a_cols = 2 * in_w;           // TMEM columns of one A stage (hi | lo)
-    const int set_cols = args.nblk * N;    // TMEM columns of one accumulator set
-    const uint32_t slab_box_bytes = (uint32_t)(kSlabRows * in_w * 4);
 
     if (tid == 0) {
         for (int s = 0; s < kRawStages; ++s) {
@@ -164,7 +171,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tmem_a = tmem;                          // A stages: [2][hi | lo]
-    const uint32_t tmem_d = tmem + (uint32_t)(2 * a_cols);  // accumulator sets: [2][nblk][N]
+    const uint32_t tmem_d = tmem + (uint32_t)(2 * A_COLS);  // accumulator sets: [2][N]
     int issued = 0;        // producer: TMA tiles issued
     int committed = -1;    // MMA issuer: last tile whose MMAs were committed
 
@@ -178,19 +185,20 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
                 if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag)) break;
-                const int X0 = (t % args.tiles_x) * (args.nblk * kNb);
-                const int Y0 = (t / args.tiles_x) * (kMathWarps * args.rows_out);
+                const int X0 = (t % args.tiles_x) * NB;
+                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
                 unsigned char* dst = raw + s * RSB;
-                ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kMathWarps * slab_box_bytes);
-                for (int q = 0; q < kMathWarps; ++q)
-                    ptx::tma_load_2d(dst + q * slab_box_bytes, &tmap, X0 - kPad, Y0 + q * args.rows_out - r, &full[s]);
+                ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
+#pragma unroll
+                for (int q = 0; q < kQuarters; ++q)
+                    ptx::tma_load_2d(dst + q * SLAB_BOX, &tmap, X0 - kPad, Y0 + q * ROWS_OUT - R, &full[s]);
                 issued = i + 1;
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
-            const uint32_t idesc = ptx::instr_desc(2, 2, 128, (uint32_t)N);
+            constexpr uint32_t idesc = ptx::instr_desc(2, 2, 128, (uint32_t)N);
             const uint32_t part_bytes = args.bop_bytes / 2;
             const uint64_t bhi0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
             const uint64_t blo0 = bhi0 + (uint64_t)(part_bytes >> 4);
@@ -201,29 +209,21 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
                 if (!wait_or_abort(&afull[st], ph, abort_flag)) break;
                 if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
                 ptx::tc_fence_after();
-                const uint32_t ahi = tmem_a + (uint32_t)(st * a_cols);
-                const uint32_t alo = ahi + (uint32_t)in_w;
-                for (int j = 0; j < args.nblk; ++j) {
-                    const uint32_t d = tmem_d + (uint32_t)(st * set_cols + j * N);
-                    const uint32_t k0 = (uint32_t)(j * kNb);
-                    if (args.nprod > 1) {
+                const uint32_t ahi = tmem_a + (uint32_t)(st * A_COLS);
+                const uint32_t alo = ahi + (uint32_t)K;
+                const uint32_t d = tmem_d + (uint32_t)(st * N);
+                if (args.nprod > 1) {
 #pragma unroll
-                        for (int ks = 0; ks < kKSteps; ++ks) {
-                            const uint64_t boff = (uint64_t)((2 * ks * N * 16) >> 4);
-                            ptx::mma_tf32_ts(d, alo + k0 + 8 * ks, bhi0 + boff, idesc, ks > 0);
-                        }
+                    for (int ks = 0; ks < KS; ++ks)
+                        ptx::mma_tf32_ts(d, alo + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, ks > 0);
 #pragma unroll
-                        for (int ks = 0; ks < kKSteps; ++ks) {
-                            const uint64_t boff = (uint64_t)((2 * ks * N * 16) >> 4);
-                            ptx::mma_tf32_ts(d, ahi + k0 + 8 * ks, blo0 + boff, idesc, 1u);
-                        }
-                    }
-#pragma unroll
-                    for (int ks = 0; ks < kKSteps; ++ks) {
-                        const uint64_t boff = (uint64_t)((2 * ks * N * 16) >> 4);
-                        ptx::mma_tf32_ts(d, ahi + k0 + 8 * ks, bhi0 + boff, idesc, (args.nprod > 1 || ks > 0) ? 1u : 0u);
-                    }
+                    for (int ks = 0; ks < KS; ++ks)
+                        ptx::mma_tf32_ts(d, ahi + 8 * ks, blo0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, 1u);
                 }
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks)
+                    ptx::mma_tf32_ts(d, ahi + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc,
+                                     (args.nprod > 1 || ks > 0) ? 1u : 0u);
                 ptx::mma_commit(&aempty[st]);
                 ptx::mma_commit(&accf[st]);
                 committed = i;
@@ -232,6 +232,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
     } else {
         // ------------------------------------------------ math warps: split + epilogue
         const int q = warp & 3;                  // TMEM lane quarter (= warp slab) of this warp
+        const int half = (warp - 2) >> 2;        // which half of the columns this warp takes
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         int i = 0, prev_t = -1;
         bool ok = true;
@@ -240,35 +241,41 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
             const uint32_t ph = (uint32_t)(ii >> 1) & 1u;
             if (!wait_or_abort(&accf[st], ph, abort_flag)) return false;
             ptx::tc_fence_after();
-            const int X0 = (tt % args.tiles_x) * (args.nblk * kNb);
-            const int Y0 = (tt / args.tiles_x) * (kMathWarps * args.rows_out);
-            const bool valid_lane = (lane >= r) && (lane < kSlabRows - r);
-            const int64_t gy = (int64_t)Y0 + q * args.rows_out + (lane - r);
-            for (int j = 0; j < args.nblk; ++j) {
-                const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * set_cols + j * N);
-                float acc[16];
+            const int X0 = (tt % args.tiles_x) * NB;
+            const int Y0 = (tt / args.tiles_x) * (kQuarters * ROWS_OUT);
+            // this warp's HALF of the tile's NB columns, for every line
+            const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + HALF * half);
+            uint32_t v[L][HALF];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
-                for (int a = 0; a < L; ++a) {
-                    uint32_t v[16];
-                    ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(a * kNb), v);
-                    ptx::tmem_wait_ld();
-                    const int src = lane + a - r;  // row this line's partial comes from
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[c]), src & 31);
-                }
-                if (valid_lane && gy < args.ny) {
-                    float* dst = args.out + gy * args.nx + X0 + j * kNb;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (X0 + j * kNb + 4 * c < args.nx)
-                            *reinterpret_cast<float4*>(dst + 4 * c) =
-                                make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-                    }
+            for (int a = 0; a < L; ++a) {
+                if constexpr (HALF == 16) {
+                    ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(a * NB), v[a]);
+                } else {
+                    ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)(a * NB), v[a]);
                 }
             }
+            ptx::tmem_wait_ld();
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&acce[st]);
+            ptx::mbar_arrive(&acce[st]);   // accumulators are in registers: the set is free
+            float acc[HALF];
+#pragma unroll
+            for (int c = 0; c < HALF; ++c) acc[c] = __uint_as_float(v[R][c]);
+#pragma unroll
+            for (int a = 0; a < L; ++a) {
+                if (a == R) continue;
+                const int src = (lane + a - R) & 31;  // row this line's partial comes from
+#pragma unroll
+                for (int c = 0; c < HALF; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[a][c]), src);
+            }
+            const int64_t gy = (int64_t)Y0 + q * ROWS_OUT + (lane - R);
+            const int gx = X0 + HALF * half;
+            if (lane >= R && lane < kSlabRows - R && gy < args.ny) {
+                float* dst = args.out + gy * args.nx + gx;
+#pragma unroll
+                for (int c = 0; c < HALF; c += 4)
+                    if (gx + c < args.nx)
+                        *reinterpret_cast<float4*>(dst + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+            }
             return true;
         };
         for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x, ++i) {
@@ -281,15 +288,16 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
                 break;
             }
             ptx::tc_fence_after();
-            const int X0 = (t % args.tiles_x) * (args.nblk * kNb);
-            const int Y0 = (t / args.tiles_x) * (kMathWarps * args.rows_out);
-            const int gy = Y0 + q * args.rows_out - r + lane;   // input row of this thread
+            const int X0 = (t % args.tiles_x) * NB;
+            const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
+            const int gy = Y0 + q * ROWS_OUT - R + lane;   // input row of this thread
             const bool fix = (args.bc == kBcPeriodic) &&
-                             (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + in_w > args.nx);
-            const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * in_w;
-            const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * a_cols);
-            const uint32_t alo = ahi + (uint32_t)in_w;
-            for (int c8 = 0; c8 < in_w; c8 += 8) {
+                             (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
+            const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
+            const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
+            const uint32_t alo = ahi + (uint32_t)K;
+#pragma unroll
+            for (int c8 = 8 * half; c8 < K; c8 += 16) {
                 float4 v0 = *reinterpret_cast<const float4*>(row + c8);
                 float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
                 if (fix) {
@@ -304,9 +312,8 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
                 uint32_t h[8], l[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const float hv = ptx::to_tf32(x[e]);
-                    h[e] = __float_as_uint(hv);
-                    l[e] = __float_as_uint(ptx::to_tf32(x[e] - hv));
+                    h[e] = tf32_hi_bits(x[e]);
+                    l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
                 }
                 ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
                 if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
@@ -345,6 +352,11 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
     }
 }
 
+template <int R>
+constexpr auto kernel_for() {
+    return mx2d_kernel<R, tile_nb(2 * R + 1)>;
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -374,6 +386,18 @@ bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+using MxKernel = void (*)(CUtensorMap, MxArgs2D);
+
+MxKernel kernel_for_radius(int r) {
+    switch (r) {
+        case 1: return kernel_for<1>();
+        case 2: return kernel_for<2>();
+        case 3: return kernel_for<3>();
+        case 4: return kernel_for<4>();
+    }
+    return nullptr;
+}
+
 // Round to TF32 on the host (nearest, ties to even); finite inputs.
 float tf32_round(float x) {
     uint32_t u;
@@ -389,7 +413,7 @@ struct MxState {
     unsigned int* err_host = nullptr;  // host-mapped error word
     unsigned int* err_dev = nullptr;
     int num_sms = 0;
-    int nblk = 2;
+    int nb = 32;          // output columns per tile
     uint32_t bop_bytes = 0;
 };
 
@@ -427,22 +451,24 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->bc = q.bc;
     p->prec = q.prec;
     p->tb = 1;
-    p->nb = kNb;
     const int W = 2 * q.r + 1;
     const int L = W;            // every row a of C^g is one line along the contiguous axis
-    const int N = L * kNb;
-    // B operand, N x K, K-major core matrices: [part][kchunk][n = a*16 + q][4];
+    const int NB = tile_nb(L);
+    const int KW = NB + 2 * kPad;
+    const int N = L * NB;
+    p->nb = NB;
+    // B operand, N x K, K-major core matrices: [part][kchunk][n = a*NB + q][4];
     // entry (n, k) = H_a[k][q] = C^g[a][k - q - (kPad - r)] (banded, Eq. (co)).
-    const size_t part_floats = (size_t)kKChunks * N * 4;
+    const size_t part_floats = (size_t)(KW / 4) * N * 4;
     std::vector<float> ops(2 * part_floats, 0.0f);
     for (int a = 0; a < L; ++a) {
-        std::vector<double> band((size_t)kK * kNb);
-        band_operand(q.r, q.cg + a * W, kNb, kPad, band.data());
-        for (int k = 0; k < kK; ++k)
-            for (int qq = 0; qq < kNb; ++qq) {
-                const float h = (float)band[(size_t)k * kNb + qq];
+        std::vector<double> band((size_t)KW * NB);
+        band_operand(q.r, q.cg + a * W, NB, kPad, band.data());
+        for (int k = 0; k < KW; ++k)
+            for (int qq = 0; qq < NB; ++qq) {
+                const float h = (float)band[(size_t)k * NB + qq];
                 const float hi = tf32_round(h);
-                const size_t off = (size_t)(k / 4) * N * 4 + (size_t)(a * kNb + qq) * 4 + (k % 4);
+                const size_t off = (size_t)(k / 4) * N * 4 + (size_t)(a * NB + qq) * 4 + (k % 4);
                 ops[off] = hi;
                 ops[part_floats + off] = tf32_round(h - hi);
             }
@@ -464,9 +490,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     }
     MxState* st = new MxState();
     st->bop_bytes = (uint32_t)p->operand_bytes;
-    // Two 16-column blocks per tile while both TMEM stages of A (2 x 2 x in_w
-    // columns) and both accumulator sets (2 x nblk x N) fit the 512 columns.
-    st->nblk = (2 * 2 * (2 * kNb + 2 * kPad) + 2 * 2 * N <= kTmemCols) ? 2 : 1;
+    st->nb = NB;
     e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
     if (e != cudaSuccess) {
@@ -486,8 +510,8 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
         if (why) *why = std::string("device query: ") + cudaGetErrorString(e);
         return STENCIL_ECUDA;
     }
-    const size_t smem = smem_bytes_2d(st->nblk * kNb + 2 * kPad, st->bop_bytes);
-    e = cudaFuncSetAttribute(mx2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = smem_bytes_2d(st->nb + 2 * kPad, st->bop_bytes);
+    e = cudaFuncSetAttribute(kernel_for_radius(q.r), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         mx_plan_free(p);
         if (why) *why = std::string("shared memory: ") + cudaGetErrorString(e);
@@ -525,21 +549,17 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.err = st->err_dev;
     a.ny = ny;
     a.nx = nx;
-    a.r = p.r;
     a.bc = p.bc;
-    a.nlines = p.n_lines;
     a.nprod = (p.prec == STENCIL_PREC_TF32X3) ? 3 : 1;
-    a.nblk = st->nblk;
-    a.in_w = st->nblk * kNb + 2 * kPad;
-    a.rows_out = kSlabRows - 2 * p.r;
-    a.tiles_x = (nx + a.nblk * kNb - 1) / (a.nblk * kNb);
-    const int tile_rows = kMathWarps * a.rows_out;
+    const int in_w = st->nb + 2 * kPad;
+    a.tiles_x = (nx + st->nb - 1) / st->nb;
+    const int tile_rows = kQuarters * (kSlabRows - 2 * p.r);
     a.tiles_total = a.tiles_x * ((ny + tile_rows - 1) / tile_rows);
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map;
-    if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, a.in_w)) return cudaErrorInvalidValue;
+    if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, in_w)) return cudaErrorInvalidValue;
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    mx2d_kernel<<<grid, kThreads, smem_bytes_2d(a.in_w, a.bop_bytes), s>>>(map, a);
+    kernel_for_radius(p.r)<<<grid, kThreads, smem_bytes_2d(in_w, a.bop_bytes), s>>>(map, a);
     return cudaGetLastError();
 }
 
