@@ -153,6 +153,30 @@ STENCIL_API stencil_status stencil_plan_info(stencil_plan_t plan, stencil_plan_i
 STENCIL_API stencil_status stencil_apply(stencil_plan_t plan, const void *d_in, void *d_out, int64_t steps,
                              stencil_stream_t stream);
 
+/* stencil_apply_noalloc -- stencil_apply for callers that cannot allocate
+ * device memory while they run steps (code inside another runtime's stream
+ * work, processes whose device memory is budgeted up front, real-time loops
+ * that cannot take cudaMalloc's synchronisation).  The paper has no
+ * counterpart: this is a deployment variant of the time loop of Sec. 2.2.
+ *
+ * Same arguments, layout and result as stencil_apply, but the second grid copy
+ * of the ping-pong is a file-scope device array of 16 MiB (4 Mi FP32 or 2 Mi
+ * FP64 points) instead of the plan's scratch grid, and the call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *   - Grids larger than 16 MiB return EINVAL with a message.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array per device and leaves its last contents
+ *     there; a sweep writes every point of the copy before reading it, so
+ *     nothing has to start at zero.  Calls whose work overlaps on the GPU (on
+ *     different streams, or while an earlier call is still running) race on
+ *     the array: order them.
+ *   - Every GPU that loads the library holds the 16 MiB until the process
+ *     exits. */
+STENCIL_API stencil_status stencil_apply_noalloc(stencil_plan_t plan, const void *d_in, void *d_out, int64_t steps,
+                                                 stencil_stream_t stream);
+
 /* Host-to-host convenience: copy h_in to the device, apply, copy the result
  * to h_out (both host arrays of the plan's dtype, pinned or pageable), and
  * synchronise.  Uses two device grids allocated per call. */

@@ -70,6 +70,7 @@ _SIGS = {
     "stencil_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(stencil_plan_info_t)]),
     "stencil_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
     "stencil_apply_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "stencil_apply_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
     "stencil_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]),
     "stencil_poll": (ctypes.c_int, [ctypes.c_uint64]),
     "stencil_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64]),
@@ -161,6 +162,10 @@ def stencil_plan_info(plan: int) -> dict:
 
 def stencil_apply(plan: int, d_in: int, d_out: int, steps: int, stream: int = 0):
     _check(lib().stencil_apply(plan, d_in, d_out, int(steps), stream), "stencil_apply")
+
+
+def stencil_apply_noalloc(plan: int, d_in: int, d_out: int, steps: int, stream: int = 0):
+    _check(lib().stencil_apply_noalloc(plan, d_in, d_out, int(steps), stream), "stencil_apply_noalloc")
 
 
 def stencil_apply_host(plan: int, h_in: np.ndarray, h_out: np.ndarray, steps: int):

@@ -319,6 +319,58 @@ extern "C" stencil_status stencil_apply_host(stencil_plan_t p, const void* h_in,
     return st;
 }
 
+// =================================================================== no-allocation apply
+//
+// A second way to run stencil_apply for callers that must not allocate device
+// memory while they step a field: for example code running inside another
+// runtime's stream-ordered work, a process whose device memory is budgeted
+// once at start-up, or a real-time loop where cudaMalloc's implicit
+// synchronisation is not acceptable.  The ping-pong copy lives in this
+// file-scope device array instead of the plan's scratch grid.  Every GPU that
+// loads the library holds the array until the process exits.
+
+static constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB: 4 Mi FP32 or 2 Mi FP64 points
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device (host code cannot use the
+// symbol itself: on the host it names a stand-in, not device memory).
+stencil_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(STENCIL_EUNSUPPORTED, "device ordinal beyond the no-allocation table");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return STENCIL_OK;
+}
+
+}  // namespace
+
+extern "C" stencil_status stencil_apply_noalloc(stencil_plan_t p, const void* d_in, void* d_out, int64_t steps,
+                                                stencil_stream_t stream) {
+    if (!p || !d_in || !d_out) return fail(STENCIL_EINVAL, "NULL argument");
+    if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    if (p->grid_bytes > kNoAllocScratchBytes)
+        return fail(STENCIL_EINVAL, "grid of " + std::to_string(p->grid_bytes) +
+                                        " bytes exceeds the 16 MiB static scratch of stencil_apply_noalloc");
+    void* scratch = nullptr;
+    stencil_status st = noalloc_scratch(&scratch);
+    if (st != STENCIL_OK) return st;
+    return time_loop(p, d_in, d_out, steps, (cudaStream_t)stream, scratch);
+}
+
 // =================================================================== async
 extern "C" stencil_status stencil_submit(stencil_plan_t p, const void* d_in, void* d_out, int64_t steps,
                                          uint64_t* ticket) {

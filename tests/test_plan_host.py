@@ -23,7 +23,7 @@ def test_library_exports_every_header_symbol():
     assert len(names) >= 14
     for n in names:
         assert hasattr(lib, n), n
-    assert set(names) <= set(sx.exported_symbols()) | {"stencil_apply_noalloc"}
+    assert set(names) <= set(sx.exported_symbols())
     assert "sm_103a" in sx.stencil_version()
 
 
