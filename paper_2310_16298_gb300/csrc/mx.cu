@@ -47,7 +47,9 @@ namespace {
 constexpr int kPad = 4;                 // input columns left/right of the output columns
 constexpr int kSlabRows = 32;           // input rows per warp slab (= TMEM lanes of one warp)
 constexpr int kQuarters = 4;            // TMEM lane quarters = warp slabs per tile
-constexpr int kMathWarps = 8;           // two per lane quarter, each taking half of the columns
+constexpr int kMathWarps = 16;          // 8 split warps + 8 epilogue warps
+constexpr int kRoleWarps = 8;           // warps per role: two per lane quarter
+constexpr int kSubs = 2;                // warps of one role per lane quarter
 constexpr int kThreads = 64 + 32 * kMathWarps;  // producer warp, MMA warp, math warps
 constexpr int kMathThreads = 32 * kMathWarps;
 constexpr int kRawStages = 6;           // TMA ring depth
@@ -72,9 +74,13 @@ struct MxArgs2D {
 
 __host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
 
+// Output staging for the TMA store: 2 stages of 4 x (32 - 2r) rows x NB
+// floats, each stage padded to 1 KB (the swizzle span).
+__host__ __device__ constexpr int out_stage_bytes(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
+
 size_t smem_bytes_2d(int in_w, uint32_t bop_bytes) {
-    return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + bop_bytes +
-           8 * (2 * kRawStages + 16);
+    return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + 2 * (size_t)out_stage_bytes(in_w - 8) +
+           bop_bytes + 8 * (2 * kRawStages + 16);
 }
 
 // Bounded mbarrier wait that also gives up once another role has failed.
@@ -102,8 +108,9 @@ __device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
 //    NB + 8 columns; slab q covers input rows Y0 + q*(32-2R) - R + [0, 32).
 //  * Warps 2..9 (two per lane quarter) split their slab into TF32 hi and lo
 //    parts and write them straight into tensor memory (tcgen05.st): the A
-//    operand never goes back through shared memory.  One tile behind, the
-//    same warps drain the accumulators and write the outputs.
+//    operand never goes back through shared memory.
+//  * Warps 10..17 (two per lane quarter) drain finished accumulators and write
+//    the outputs, concurrently with the split of later tiles.
 //  * Warp 1 issues the outer products.  All 2R+1 coefficient lines of the
 //    stencil sit side by side along N (B = [H_0 | ... | H_2R], N = NB (2R+1)),
 //    so one tcgen05.mma applies every line to the same input rows; line a's
@@ -117,21 +124,25 @@ __device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
 //    epilogue.
 template <int R, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
-mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
+mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
+            const MxArgs2D args) {
     constexpr int L = 2 * R + 1;            // lines
     constexpr int N = L * NB;               // MMA N
     constexpr int K = NB + 2 * kPad;        // input columns per tile = K window
     constexpr int KS = K / 8;               // tf32 MMAs per window
     constexpr int ROWS_OUT = kSlabRows - 2 * R;
     constexpr int A_COLS = 2 * K;           // TMEM columns of one A stage (hi | lo)
-    constexpr int HALF = NB / 2;            // epilogue columns per math warp
+    constexpr int CW = NB / kSubs;          // epilogue columns per epilogue warp
+    constexpr int NG = K / 8;               // 8-column groups of the input tile
     constexpr int RSB = raw_stage_bytes(K);
     constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* raw = smem;                                // kRawStages tiles
+    constexpr int OSB = out_stage_bytes(NB);
+    unsigned char* outs = smem;                               // 2 output stages (1 KB aligned)
+    unsigned char* raw = outs + 2 * OSB;                      // kRawStages tiles
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;                          // [kRawStages] TMA landed
@@ -141,24 +152,27 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
     uint64_t* accf = aempty + 2;                    // [2] accumulator set ready
     uint64_t* acce = accf + 2;                      // [2] accumulator set drained
     uint64_t* bop_bar = acce + 2;
-    uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
+    uint64_t* osync = bop_bar + 1;                  // epilogue warps: output-stage hand-offs
+    uint32_t* tmem_slot = (uint32_t*)(osync + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
+        // split/epilogue barriers count one (elected) arrival per warp of the role
         for (int s = 0; s < kRawStages; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&rawfree[s], kMathThreads);
+            ptx::mbar_init(&rawfree[s], kRoleWarps);
         }
         for (int a = 0; a < 2; ++a) {
-            ptx::mbar_init(&afull[a], kMathThreads);
+            ptx::mbar_init(&afull[a], kRoleWarps);
             ptx::mbar_init(&aempty[a], 1);
             ptx::mbar_init(&accf[a], 1);
-            ptx::mbar_init(&acce[a], kMathThreads);
+            ptx::mbar_init(&acce[a], kRoleWarps);
         }
         ptx::mbar_init(bop_bar, 1);
+        ptx::mbar_init(osync, kRoleWarps);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -230,108 +244,133 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const MxArgs2D args) {
             }
         }
     } else {
-        // ------------------------------------------------ math warps: split + epilogue
-        const int q = warp & 3;                  // TMEM lane quarter (= warp slab) of this warp
-        const int half = (warp - 2) >> 2;        // which half of the columns this warp takes
+        // ------------------------------------------------ math warps
+        const int q = warp & 3;                        // TMEM lane quarter (= warp slab) of this warp
+        const bool split_role = (warp - 2) < kRoleWarps;
+        const int sub = ((warp - 2) >> 2) & 1;         // which half of the role's work this warp takes
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        int i = 0, prev_t = -1;
-        bool ok = true;
-        auto epilogue = [&](int ii, int tt) -> bool {
-            const int st = ii & 1;
-            const uint32_t ph = (uint32_t)(ii >> 1) & 1u;
-            if (!wait_or_abort(&accf[st], ph, abort_flag)) return false;
-            ptx::tc_fence_after();
-            const int X0 = (tt % args.tiles_x) * NB;
-            const int Y0 = (tt / args.tiles_x) * (kQuarters * ROWS_OUT);
-            // this warp's HALF of the tile's NB columns, for every line
-            const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + HALF * half);
-            uint32_t v[L][HALF];
+        if (split_role) {
+            // ---------------- split: raw tile (smem) -> TF32 hi/lo A operand (TMEM)
+            int i = 0;
+            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+                const int rs = i % kRawStages;
+                const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
+                const int st = i & 1;
+                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[st], ph ^ 1u, abort_flag))
+                    break;
+                ptx::tc_fence_after();
+                const int X0 = (t % args.tiles_x) * NB;
+                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
+                const int gy = Y0 + q * ROWS_OUT - R + lane;   // input row of this thread
+                const bool fix = (args.bc == kBcPeriodic) &&
+                                 (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
+                const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
+                const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
+                const uint32_t alo = ahi + (uint32_t)K;
 #pragma unroll
-            for (int a = 0; a < L; ++a) {
-                if constexpr (HALF == 16) {
-                    ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(a * NB), v[a]);
-                } else {
-                    ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)(a * NB), v[a]);
+                for (int g0 = 0; g0 < NG; g0 += kSubs) {
+                    const int g = g0 + sub;
+                    if (g >= NG) break;
+                    const int c8 = 8 * g;
+                    float4 v0 = *reinterpret_cast<const float4*>(row + c8);
+                    float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
+                    if (fix) {
+                        const int64_t wy = wrap_index(gy, args.ny);
+                        const int gx0 = X0 - kPad + c8;
+                        if (gy < 0 || gy >= args.ny || gx0 < 0 || gx0 >= args.nx)
+                            v0 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0, args.nx));
+                        if (gy < 0 || gy >= args.ny || gx0 + 4 < 0 || gx0 + 4 >= args.nx)
+                            v1 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0 + 4, args.nx));
+                    }
+                    const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    uint32_t h[8], l[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        h[e] = tf32_hi_bits(x[e]);
+                        l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+                    }
+                    ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
+                    if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
+                }
+                ptx::tmem_wait_st();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    ptx::mbar_arrive(&rawfree[rs]);
+                    ptx::mbar_arrive(&afull[st]);
                 }
             }
-            ptx::tmem_wait_ld();
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&acce[st]);   // accumulators are in registers: the set is free
-            float acc[HALF];
+        } else {
+            // ---------------- epilogue: accumulators (TMEM) -> row shifts -> outputs (global)
+            int i = 0;
+            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+                const int st = i & 1;
+                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                if (!wait_or_abort(&accf[st], ph, abort_flag)) break;
+                ptx::tc_fence_after();
+                const int X0 = (t % args.tiles_x) * NB;
+                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
+                // this warp's CW of the tile's NB columns, for every line
+                const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + CW * sub);
+                uint32_t v[L][CW];
 #pragma unroll
-            for (int c = 0; c < HALF; ++c) acc[c] = __uint_as_float(v[R][c]);
-#pragma unroll
-            for (int a = 0; a < L; ++a) {
-                if (a == R) continue;
-                const int src = (lane + a - R) & 31;  // row this line's partial comes from
-#pragma unroll
-                for (int c = 0; c < HALF; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[a][c]), src);
-            }
-            const int64_t gy = (int64_t)Y0 + q * ROWS_OUT + (lane - R);
-            const int gx = X0 + HALF * half;
-            if (lane >= R && lane < kSlabRows - R && gy < args.ny) {
-                float* dst = args.out + gy * args.nx + gx;
-#pragma unroll
-                for (int c = 0; c < HALF; c += 4)
-                    if (gx + c < args.nx)
-                        *reinterpret_cast<float4*>(dst + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
-            }
-            return true;
-        };
-        for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x, ++i) {
-            const int rs = i % kRawStages;
-            const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
-            const int st = i & 1;
-            const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-            if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[st], ph ^ 1u, abort_flag)) {
-                ok = false;
-                break;
-            }
-            ptx::tc_fence_after();
-            const int X0 = (t % args.tiles_x) * NB;
-            const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
-            const int gy = Y0 + q * ROWS_OUT - R + lane;   // input row of this thread
-            const bool fix = (args.bc == kBcPeriodic) &&
-                             (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
-            const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
-            const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
-            const uint32_t alo = ahi + (uint32_t)K;
-#pragma unroll
-            for (int c8 = 8 * half; c8 < K; c8 += 16) {
-                float4 v0 = *reinterpret_cast<const float4*>(row + c8);
-                float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
-                if (fix) {
-                    const int64_t wy = wrap_index(gy, args.ny);
-                    const int gx0 = X0 - kPad + c8;
-                    if (gy < 0 || gy >= args.ny || gx0 < 0 || gx0 >= args.nx)
-                        v0 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0, args.nx));
-                    if (gy < 0 || gy >= args.ny || gx0 + 4 < 0 || gx0 + 4 >= args.nx)
-                        v1 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0 + 4, args.nx));
+                for (int a = 0; a < L; ++a) {
+                    if constexpr (CW == 16) {
+                        ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(a * NB), v[a]);
+                    } else {
+                        ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)(a * NB), v[a]);
+                    }
                 }
-                const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                uint32_t h[8], l[8];
+                ptx::tmem_wait_ld();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&acce[st]);   // accumulators are in registers: the set is free
+                float acc[CW];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    h[e] = tf32_hi_bits(x[e]);
-                    l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+                for (int c = 0; c < CW; ++c) acc[c] = __uint_as_float(v[R][c]);
+#pragma unroll
+                for (int a = 0; a < L; ++a) {
+                    if (a == R) continue;
+                    const int src = (lane + a - R) & 31;  // row this line's partial comes from
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[a][c]), src);
                 }
-                ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
-                if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
+                // Stage the outputs row-major in shared memory with the TMA
+                // swizzle (16-byte chunk index XOR row bits), then one thread
+                // writes the whole tile with a single TMA store.
+                unsigned char* ost = outs + st * OSB;
+                const bool issuer = (warp == 2 + kRoleWarps) && lane == 0;
+                if (issuer) ptx::bulk_wait_group_read<1>();   // the store that used this stage two tiles ago
+                // hand-off 1: the stage is free (bounded wait on an mbarrier, two phases per tile)
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(osync);
+                if (!wait_or_abort(osync, 0u, abort_flag)) break;
+                if (lane >= R && lane < kSlabRows - R) {
+                    const int orow = q * ROWS_OUT + (lane - R);
+#pragma unroll
+                    for (int c = 0; c < CW; c += 4) {
+                        const int chunk = (CW * sub + c) >> 2;
+                        const int sw = (NB == 32) ? (chunk ^ (orow & 7)) : (chunk ^ ((orow >> 1) & 3));
+                        *reinterpret_cast<float4*>(ost + orow * (NB * 4) + sw * 16) =
+                            make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                    }
+                }
+                ptx::fence_proxy_async_smem();
+                // hand-off 2: every warp's outputs are in the stage
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(osync);
+                if (!wait_or_abort(osync, 1u, abort_flag)) break;
+                if (issuer) {
+                    ptx::tma_store_2d(&tmap_out, X0, Y0, ost);
+                    ptx::bulk_commit_group();
+                }
             }
-            ptx::tmem_wait_st();
-            ptx::mbar_arrive(&rawfree[rs]);
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&afull[st]);
-            if (prev_t >= 0 && !epilogue(i - 1, prev_t)) {
-                ok = false;
-                break;
-            }
-            prev_t = t;
         }
-        if (ok && prev_t >= 0) epilogue(i - 1, prev_t);
     }
 
     // ---- teardown (also after an abort: every role has left its loop)
+    if (warp == 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
     if (*abort_flag) {
         // Let copies and MMAs still in flight land before the CTA gives up its
         // shared and tensor memory (each wait bounded again).
@@ -386,7 +425,22 @@ bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-using MxKernel = void (*)(CUtensorMap, MxArgs2D);
+// Row-major 2D view of the output grid; one box is a whole output tile
+// (NB columns x 4 (32-2r) rows), written from shared memory with the TMA
+// 128-byte (NB = 32) or 64-byte (NB = 16) swizzle.
+bool encode_out_map_2d(CUtensorMap* map, float* base, int ny, int nx, int nb, int rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+    cuuint32_t box[2] = {(cuuint32_t)nb, (cuuint32_t)rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, nb == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+using MxKernel = void (*)(CUtensorMap, CUtensorMap, MxArgs2D);
 
 MxKernel kernel_for_radius(int r) {
     switch (r) {
@@ -557,9 +611,11 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.tiles_total = a.tiles_x * ((ny + tile_rows - 1) / tile_rows);
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map;
+    alignas(64) CUtensorMap map_out;
     if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, in_w)) return cudaErrorInvalidValue;
+    if (!encode_out_map_2d(&map_out, (float*)dst, ny, nx, st->nb, tile_rows)) return cudaErrorInvalidValue;
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    kernel_for_radius(p.r)<<<grid, kThreads, smem_bytes_2d(in_w, a.bop_bytes), s>>>(map, a);
+    kernel_for_radius(p.r)<<<grid, kThreads, smem_bytes_2d(in_w, a.bop_bytes), s>>>(map, map_out, a);
     return cudaGetLastError();
 }
 
