@@ -37,9 +37,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--side", type=int, default=8192)
-    ap.add_argument("--tsteps", type=int, default=100, help="stencil time steps per solve")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--workload", default="box25-8192",
+                    choices=["box25-8192", "star7-512", "box27-512", "jacobi-256"])
+    ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
+    ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
+    ap.add_argument("--dtype", default="", choices=["", "f32", "f64"], help="storage type ('' = the workload's own)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -54,15 +56,28 @@ def dist_env():
 
 def workload(args):
     import stencil_inputs as si
-    return si.box25_8192(args.dtype, args.tsteps, args.side)
+    w = args.workload
+    if w == "box25-8192":
+        return si.box25_8192(args.dtype or "f32", args.tsteps or 100, args.side or 8192)
+    if w == "star7-512":
+        return si.cube_512(si.STAR, args.dtype or "f32", args.tsteps or 50, args.side or 512)
+    if w == "box27-512":
+        return si.cube_512(si.BOX, args.dtype or "f32", args.tsteps or 50, args.side or 512)
+    p = si.jacobi_256(args.tsteps or 10)
+    return p
 
 
 def workload_config(p, args, extra=None):
-    cfg = {"workload": f"2D box r=2 (25-point) {p.shape[0]}x{p.shape[1]} {args.dtype.upper()}, "
-                       f"periodic, {p.steps} time steps per solve, uniform[0,1) coefficients normalised to 1",
+    desc = {"box25-8192": "2D box r=2 (25-point)", "star7-512": "3D 7-point star", "box27-512": "3D 27-point box",
+            "jacobi-256": "2D 5-point Jacobi star"}[args.workload]
+    grid_bytes = p.points * (4 if p.dtype == "f32" else 8)
+    cfg = {"workload": f"{desc} {'x'.join(str(s) for s in p.shape)} {p.dtype.upper()}, {p.bc}, "
+                       f"{p.steps} time steps per solve, seeded synthetic field and coefficients",
            "grid": list(p.shape), "radius": p.r, "kind": p.kind, "boundary": p.bc,
            "time_steps_per_solve": p.steps,
-           "l2_policy": "inputs larger than L2 (grid 256 MiB FP32 > 129 MB L2); no flush"}
+           "l2_policy": (f"inputs larger than L2 (grid {grid_bytes / 2**20:.0f} MiB > 129 MB L2); no flush"
+                         if grid_bytes > 129e6 else
+                         f"grid {grid_bytes / 2**20:.1f} MiB is L2-resident: latency workload, no HBM claim")}
     if extra:
         cfg.update(extra)
     return cfg
@@ -171,7 +186,7 @@ def oracle_baseline(p, field, max_seconds=20.0):
         nsteps, dt = 1, t1
     gst = p.points * nsteps / dt / 1e9
     return {"value": gst, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"full {p.shape[0]}x{p.shape[1]} grid, {nsteps} of {p.steps} time steps, "
+            "sample": f"full {'x'.join(str(s) for s in p.shape)} grid, {nsteps} of {p.steps} time steps, "
                       f"{dt:.1f} s, FP64 gather definition, OpenMP over rows"}
 
 
@@ -325,7 +340,7 @@ def main():
     alg_bytes = 2 * es * p.points  # read the grid once, write it once per launch
     pk = peaks()
     achieved = alg_bytes / (kms / 1e3) / 1e9
-    kernel_key = f"{main_impl}-{p.dtype}-2d-r{p.r}-{p.kind}-tb{tb}"
+    kernel_key = f"{main_impl}-{p.dtype}-{p.ndim}d-r{p.r}-{p.kind}-tb{tb}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(kernel_key),
                 "kernel": kernel_key, "launch_ms": kms, "algorithmic_bytes_per_launch": alg_bytes,

@@ -39,10 +39,13 @@
 #include "mx.h"
 #include "plan.h"
 #include "ptx.cuh"
+#include "mxutil.cuh"
 
 namespace stx {
 
 namespace {
+
+using namespace mxu;
 
 constexpr int kPad = 4;                 // input columns left/right of the output columns
 constexpr int kSlabRows = 32;           // input rows per warp slab (= TMEM lanes of one warp)
@@ -54,7 +57,6 @@ constexpr int kThreads = 64 + 32 * kMathWarps;  // producer warp, MMA warp, math
 constexpr int kMathThreads = 32 * kMathWarps;
 constexpr int kRawStages = 6;           // TMA ring depth
 constexpr int kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // Output columns per tile (the MMA block width) for a stencil with L lines:
 // 32 while both accumulator sets (2 x L x 32 columns) and both A stages
@@ -81,25 +83,6 @@ __host__ __device__ constexpr int out_stage_bytes(int nb) { return ((4 * 32 * nb
 size_t smem_bytes_2d(int in_w, uint32_t bop_bytes) {
     return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + 2 * (size_t)out_stage_bytes(in_w - 8) +
            bop_bytes + 8 * (2 * kRawStages + 16);
-}
-
-// Bounded mbarrier wait that also gives up once another role has failed.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    const long long t0 = clock64();
-    while (!ptx::mbar_try_wait(bar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-// TF32 high part by integer rounding (nearest, ties away from zero): the low
-// 13 mantissa bits are cleared after adding half of their weight.
-__device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
-    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 // Persistent, warp-specialised sweep (R = order; NB = output columns per tile).
@@ -397,20 +380,6 @@ constexpr auto kernel_for() {
 }
 
 // ------------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
 // Row-major 2D view of the grid; one box is a 32-row slab of an input tile
 // (in_w columns, in_w*4-byte TMA rows).
 bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int in_w) {
@@ -452,17 +421,6 @@ MxKernel kernel_for_radius(int r) {
     return nullptr;
 }
 
-// Round to TF32 on the host (nearest, ties to even); finite inputs.
-float tf32_round(float x) {
-    uint32_t u;
-    memcpy(&u, &x, 4);
-    u += 0xFFFu + ((u >> 13) & 1u);
-    u &= ~0x1FFFu;
-    float y;
-    memcpy(&y, &u, 4);
-    return y;
-}
-
 struct MxState {
     unsigned int* err_host = nullptr;  // host-mapped error word
     unsigned int* err_dev = nullptr;
@@ -478,10 +436,7 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "FP64 storage runs on the CUDA-core kernel (no FP64 tensor-core path on this GPU)";
         return false;
     }
-    if (q.ndim != 2) {
-        if (why) *why = "3D matrixized kernel not built";
-        return false;
-    }
+    if (q.ndim == 3) return mx3d_supported(q, why);
     if (q.prec != STENCIL_PREC_TF32 && q.prec != STENCIL_PREC_TF32X3) {
         if (why) *why = "only TF32 and TF32X3 outer products are built for 2D";
         return false;
@@ -505,6 +460,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->bc = q.bc;
     p->prec = q.prec;
     p->tb = 1;
+    if (q.ndim == 3) return mx3d_plan_build(q, p, why);
     const int W = 2 * q.r + 1;
     const int L = W;            // every row a of C^g is one line along the contiguous axis
     const int NB = tile_nb(L);
@@ -575,6 +531,10 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
 }
 
 void mx_plan_free(MxPlan* p) {
+    if (p->ndim == 3) {
+        mx3d_plan_free(p);
+        return;
+    }
     if (p->d_operands) cudaFree(p->d_operands);
     p->d_operands = nullptr;
     MxState* st = (MxState*)p->tmap_storage;
@@ -586,11 +546,13 @@ void mx_plan_free(MxPlan* p) {
 }
 
 unsigned int mx_device_error(const MxPlan& p) {
+    if (p.ndim == 3) return mx3d_device_error(p);
     const MxState* st = (const MxState*)p.tmap_storage;
     return st && st->err_host ? *(volatile unsigned int*)st->err_host : 0u;
 }
 
 cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s) {
+    if (p.ndim == 3) return mx3d_sweep(p, src, dst, tb, s);
     if (tb != 1) return cudaErrorInvalidValue;
     if (((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return cudaErrorMisalignedAddress;
     const MxState* st = (const MxState*)p.tmap_storage;

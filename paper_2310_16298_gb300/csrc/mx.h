@@ -40,6 +40,13 @@ struct MxPlan {
 };
 
 bool mx_supported(const MxRequest& q, std::string* why);
+
+// 3D kernels (mx3d.cu); the mx_* entry points dispatch to them for ndim == 3.
+bool mx3d_supported(const MxRequest& q, std::string* why);
+stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why);
+void mx3d_plan_free(MxPlan* p);
+cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
+unsigned int mx3d_device_error(const MxPlan& p);
 stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why);
 void mx_plan_free(MxPlan* p);
 cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);

@@ -1,0 +1,573 @@
+// Matrixized 3D stencil sweep on tcgen05 tensor cores.
+//
+// The grid is swept plane by plane along the slowest axis z, following the
+// structure of Algorithm 1: every input plane is loaded once and scattered to
+// the 2R+1 output planes it contributes to.  Within a plane the coefficient
+// lines run along the contiguous axis x: line (a, b) holds the weights
+// C^g[a][b][*] (a = z offset, b = y offset) as a banded operand H_ab, exactly
+// as the 2D kernel uses one line per y offset.  All lines of the stencil sit
+// side by side along the MMA's N dimension, so one tcgen05.mma (128 rows x
+// N x 8) applies every line to one input plane; the epilogue then shifts each
+// line's partial sums by b - R rows (warp shuffles) and adds them, in FP32
+// round-to-nearest registers, to the running sum of output plane
+// z - (a - R).  When input plane z has been scattered, output plane z - R is
+// complete and is written with one TMA store.
+//
+// Work unit = (32-row-slab tile in y, NB columns in x, a chunk of output
+// planes in z); the unit streams its chunk plus R halo planes on either side.
+// Roles per CTA as in the 2D kernel: TMA producer warp, MMA warp, 8 split
+// warps (input plane -> TF32 hi/lo A operand in tensor memory), 8 epilogue
+// warps (tensor memory -> plane accumulators -> TMA store).
+#include <cuda.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "mx.h"
+#include "mxutil.cuh"
+#include "plan.h"
+#include "ptx.cuh"
+
+namespace stx {
+
+namespace {
+
+using namespace mxu;
+
+constexpr int kPad = 4;
+constexpr int kSlabRows = 32;
+constexpr int kQuarters = 4;
+constexpr int kRoleWarps = 8;
+constexpr int kSubs = 2;
+constexpr int kMathWarps = 2 * kRoleWarps;
+constexpr int kThreads = 64 + 32 * kMathWarps;
+constexpr int kRawStages = 6;
+constexpr int kTmemCols = 512;
+constexpr int kChunk = 32;  // output planes per work unit
+
+// Coefficient lines of a 3D stencil: (a = z offset, b = y offset) pairs that
+// carry weights.  Box: all (2R+1)^2 pairs.  Star: (a, R) for a != R and
+// (R, b) for every b; the centre weight sits on line (R, R).
+template <int R, bool STAR>
+struct Lines3 {
+    static constexpr int W = 2 * R + 1;
+    static constexpr int L = STAR ? (4 * R + 1) : W * W;
+    __host__ __device__ static constexpr int a(int l) {
+        return STAR ? (l < R ? l : (l < R + W ? R : l - W + 1)) : l / W;
+    }
+    __host__ __device__ static constexpr int b(int l) { return STAR ? (l < R || l >= R + W ? R : l - R) : l % W; }
+};
+
+__host__ __device__ constexpr int tile_nb3(int L) { return (2 * L * 32 + 4 * (32 + 2 * kPad) <= kTmemCols) ? 32 : 16; }
+__host__ __device__ constexpr int raw_stage_bytes3(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
+__host__ __device__ constexpr int out_stage_bytes3(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
+
+size_t smem_bytes_3d(int in_w, uint32_t bop_bytes) {
+    return 1024 + (size_t)kRawStages * raw_stage_bytes3(in_w) + 2 * (size_t)out_stage_bytes3(in_w - 8) + bop_bytes +
+           8 * (2 * kRawStages + 16);
+}
+
+struct MxArgs3D {
+    const float* bops;    // banded operands [part][kchunk][line*NB + q][4]
+    unsigned int* err;    // device error word (host-mapped)
+    int nz, ny, nx;
+    int nprod;            // 1 (TF32) or 3 (TF32x3)
+    int tiles_x, tiles_y, chunks, units;
+    uint32_t bop_bytes;
+};
+
+template <int R, bool STAR, int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
+            const MxArgs3D args) {
+    using LN = Lines3<R, STAR>;
+    constexpr int L = LN::L;
+    constexpr int N = L * NB;
+    constexpr int K = NB + 2 * kPad;
+    constexpr int KS = K / 8;
+    constexpr int NG = K / 8;
+    constexpr int ROWS_OUT = kSlabRows - 2 * R;
+    constexpr int A_COLS = 2 * K;
+    constexpr int CW = NB / kSubs;
+    constexpr int RSB = raw_stage_bytes3(K);
+    constexpr int OSB = out_stage_bytes3(NB);
+    constexpr int PLANES = kChunk + 2 * R;  // input planes per work unit
+    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
+    static_assert(N <= 256 && N % 16 == 0, "MMA N");
+    static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* outs = smem;
+    unsigned char* raw = outs + 2 * OSB;
+    unsigned char* bops = raw + kRawStages * RSB;
+    uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
+    uint64_t* full = bars;
+    uint64_t* rawfree = bars + kRawStages;
+    uint64_t* afull = bars + 2 * kRawStages;
+    uint64_t* aempty = afull + 2;
+    uint64_t* accf = aempty + 2;
+    uint64_t* acce = accf + 2;
+    uint64_t* bop_bar = acce + 2;
+    uint64_t* osync = bop_bar + 1;
+    uint32_t* tmem_slot = (uint32_t*)(osync + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < kRawStages; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&rawfree[s], kRoleWarps);
+        }
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(&afull[a], kRoleWarps);
+            ptx::mbar_init(&aempty[a], 1);
+            ptx::mbar_init(&accf[a], 1);
+            ptx::mbar_init(&acce[a], kRoleWarps);
+        }
+        ptx::mbar_init(bop_bar, 1);
+        ptx::mbar_init(osync, kRoleWarps);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, kTmemCols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem_a = tmem;
+    const uint32_t tmem_d = tmem + (uint32_t)(2 * A_COLS);
+    int issued = 0, committed = -1;
+
+    // unit u -> (x tile, y tile, z chunk), x fastest
+    auto unit_origin = [&](int u, int& X0, int& Y0, int& Z0) {
+        X0 = (u % args.tiles_x) * NB;
+        Y0 = ((u / args.tiles_x) % args.tiles_y) * (kQuarters * ROWS_OUT);
+        Z0 = (u / (args.tiles_x * args.tiles_y)) * kChunk;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            ptx::mbar_arrive_expect_tx(bop_bar, args.bop_bytes);
+            ptx::bulk_load(bops, args.bops, args.bop_bytes, bop_bar);
+            int i = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+                int X0, Y0, Z0;
+                unit_origin(u, X0, Y0, Z0);
+                for (int iz = 0; iz < PLANES; ++iz, ++i) {
+                    const int s = i % kRawStages;
+                    const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
+                    if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* dst = raw + s * RSB;
+                    ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
+#pragma unroll
+                    for (int q = 0; q < kQuarters; ++q)
+                        ptx::tma_load_3d(dst + q * SLAB_BOX, &tmap, X0 - kPad, Y0 + q * ROWS_OUT - R, Z0 - R + iz,
+                                         &full[s]);
+                    issued = i + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
+            constexpr uint32_t idesc = ptx::instr_desc(2, 2, 128, (uint32_t)N);
+            const uint32_t part_bytes = args.bop_bytes / 2;
+            const uint64_t bhi0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
+            const uint64_t blo0 = bhi0 + (uint64_t)(part_bytes >> 4);
+            int i = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+                for (int iz = 0; iz < PLANES; ++iz, ++i) {
+                    const int st = i & 1;
+                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                    if (!wait_or_abort(&afull[st], ph, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t ahi = tmem_a + (uint32_t)(st * A_COLS);
+                    const uint32_t alo = ahi + (uint32_t)K;
+                    const uint32_t d = tmem_d + (uint32_t)(st * N);
+                    if (args.nprod > 1) {
+#pragma unroll
+                        for (int ks = 0; ks < KS; ++ks)
+                            ptx::mma_tf32_ts(d, alo + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, ks > 0);
+#pragma unroll
+                        for (int ks = 0; ks < KS; ++ks)
+                            ptx::mma_tf32_ts(d, ahi + 8 * ks, blo0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, 1u);
+                    }
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks)
+                        ptx::mma_tf32_ts(d, ahi + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc,
+                                         (args.nprod > 1 || ks > 0) ? 1u : 0u);
+                    ptx::mma_commit(&aempty[st]);
+                    ptx::mma_commit(&accf[st]);
+                    committed = i;
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const bool split_role = (warp - 2) < kRoleWarps;
+        const int sub = ((warp - 2) >> 2) & 1;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        int i = 0;
+        bool ok = true;
+        if (split_role) {
+            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+                for (int iz = 0; iz < PLANES; ++iz, ++i) {
+                    const int rs = i % kRawStages;
+                    const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
+                    const int st = i & 1;
+                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                    if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[st], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
+                    const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
+                    const uint32_t alo = ahi + (uint32_t)K;
+#pragma unroll
+                    for (int g0 = 0; g0 < NG; g0 += kSubs) {
+                        const int g = g0 + sub;
+                        if (g >= NG) break;
+                        const int c8 = 8 * g;
+                        const float4 v0 = *reinterpret_cast<const float4*>(row + c8);
+                        const float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
+                        const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                        uint32_t h[8], l[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            h[e] = tf32_hi_bits(x[e]);
+                            l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+                        }
+                        ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
+                        if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
+                    }
+                    ptx::tmem_wait_st();
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        ptx::mbar_arrive(&rawfree[rs]);
+                        ptx::mbar_arrive(&afull[st]);
+                    }
+                }
+            }
+        } else {
+            const bool issuer = (warp == 2 + kRoleWarps) && lane == 0;
+            int nstore = 0;
+            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+                int X0, Y0, Z0;
+                unit_origin(u, X0, Y0, Z0);
+                float acc[2 * R + 1][CW];  // running sums of output planes z-R .. z+R
+#pragma unroll
+                for (int j = 0; j < 2 * R + 1; ++j)
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) acc[j][c] = 0.0f;
+                for (int iz = 0; iz < PLANES; ++iz, ++i) {
+                    const int st = i & 1;
+                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                    if (!wait_or_abort(&accf[st], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + CW * sub);
+                    // line (a, b): rows shift by b - R, target output plane slot 2R - a.
+                    // Lines are drained in batches of LB to bound live registers.
+                    constexpr int LB = (CW == 16) ? 2 : 4;
+#pragma unroll
+                    for (int l0 = 0; l0 < L; l0 += LB) {
+                        uint32_t v[LB][CW];
+#pragma unroll
+                        for (int j = 0; j < LB; ++j) {
+                            if (l0 + j < L) {
+                                if constexpr (CW == 16) {
+                                    ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((l0 + j) * NB), v[j]);
+                                } else {
+                                    ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)((l0 + j) * NB), v[j]);
+                                }
+                            }
+                        }
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < LB; ++j) {
+                            const int l = l0 + j;
+                            if (l < L) {
+                                const int la = LN::a(l), lb = LN::b(l);
+                                const int src = (lane + lb - R) & 31;
+#pragma unroll
+                                for (int c = 0; c < CW; ++c) {
+                                    const float val = (lb == R) ? __uint_as_float(v[j][c])
+                                                                : __shfl_sync(0xffffffffu, __uint_as_float(v[j][c]), src);
+                                    acc[2 * R - la][c] += val;
+                                }
+                            }
+                        }
+                    }
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&acce[st]);
+                    if (iz >= 2 * R) {
+                        // output plane Z0 + iz - 2R is complete: stage it and store it
+                        unsigned char* ost = outs + (nstore & 1) * OSB;
+                        if (issuer) ptx::bulk_wait_group_read<1>();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(osync);
+                        if (!wait_or_abort(osync, 0u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        if (lane >= R && lane < kSlabRows - R) {
+                            const int orow = q * ROWS_OUT + (lane - R);
+#pragma unroll
+                            for (int c = 0; c < CW; c += 4) {
+                                const int chunk = (CW * sub + c) >> 2;
+                                const int sw = (NB == 32) ? (chunk ^ (orow & 7)) : (chunk ^ ((orow >> 1) & 3));
+                                *reinterpret_cast<float4*>(ost + orow * (NB * 4) + sw * 16) =
+                                    make_float4(acc[0][c], acc[0][c + 1], acc[0][c + 2], acc[0][c + 3]);
+                            }
+                        }
+                        ptx::fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(osync);
+                        if (!wait_or_abort(osync, 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        if (issuer) {
+                            ptx::tma_store_3d(&tmap_out, X0, Y0, Z0 + iz - 2 * R, ost);
+                            ptx::bulk_commit_group();
+                        }
+                        ++nstore;
+                    }
+                    // slide the window of output planes by one
+#pragma unroll
+                    for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+                        for (int c = 0; c < CW; ++c) acc[j][c] = acc[j + 1][c];
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) acc[2 * R][c] = 0.0f;
+                }
+            }
+        }
+    }
+
+    if (warp == 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();
+    if (*abort_flag) {
+        if (warp == 0 && lane == 0) {
+            for (int k = issued - kRawStages; k < issued; ++k)
+                if (k >= 0) ptx::mbar_wait(&full[k % kRawStages], (uint32_t)(k / kRawStages) & 1u, kWaitCycles / 8);
+        }
+        if (warp == 1 && lane == 0 && committed >= 0)
+            ptx::mbar_wait(&accf[committed & 1], (uint32_t)(committed >> 1) & 1u, kWaitCycles / 8);
+    }
+    __syncwarp();
+    if (tid == 0 && *abort_flag) atomicOr(args.err, 1u);
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+using Mx3Kernel = void (*)(CUtensorMap, CUtensorMap, MxArgs3D);
+
+template <int R, bool STAR>
+Mx3Kernel kernel3() {
+    return mx3d_kernel<R, STAR, tile_nb3(Lines3<R, STAR>::L)>;
+}
+
+Mx3Kernel kernel3_for(int r, bool star) {
+    if (star) {
+        switch (r) {
+            case 1: return kernel3<1, true>();
+            case 2: return kernel3<2, true>();
+            case 3: return kernel3<3, true>();
+        }
+    } else if (r == 1) {
+        return kernel3<1, false>();
+    }
+    return nullptr;
+}
+
+int lines3(int r, bool star) { return star ? 4 * r + 1 : (2 * r + 1) * (2 * r + 1); }
+int line3_a(int r, bool star, int l) {
+    const int W = 2 * r + 1;
+    return star ? (l < r ? l : (l < r + W ? r : l - W + 1)) : l / W;
+}
+int line3_b(int r, bool star, int l) {
+    const int W = 2 * r + 1;
+    return star ? (l < r || l >= r + W ? r : l - r) : l % W;
+}
+
+bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int nx, int in_w) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)in_w, (cuuint32_t)kSlabRows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, int nb, int rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)nb, (cuuint32_t)rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, nb == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct Mx3State {
+    unsigned int* err_host = nullptr;
+    unsigned int* err_dev = nullptr;
+    int num_sms = 0;
+    int nb = 16;
+    bool star = false;
+    uint32_t bop_bytes = 0;
+};
+
+}  // namespace
+
+bool mx3d_supported(const MxRequest& q, std::string* why) {
+    if (q.prec != STENCIL_PREC_TF32 && q.prec != STENCIL_PREC_TF32X3) {
+        if (why) *why = "only TF32 and TF32X3 outer products are built for 3D";
+        return false;
+    }
+    if (q.bc != kBcDirichlet) {
+        if (why) *why = "the 3D matrixized kernel handles the zero Dirichlet boundary only";
+        return false;
+    }
+    if (!kernel3_for(q.r, q.star)) {
+        if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27-point box";
+        return false;
+    }
+    if (q.n[2] % 4 != 0) {
+        if (why) *why = "the contiguous extent must be a multiple of 4 (16-byte TMA rows)";
+        return false;
+    }
+    if (q.tb > 1) {
+        if (why) *why = "temporal blocking not built for the matrixized kernel";
+        return false;
+    }
+    return true;
+}
+
+stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
+    if (!mx3d_supported(q, why)) return STENCIL_EUNSUPPORTED;
+    const int r = q.r, W = 2 * r + 1;
+    const int L = lines3(r, q.star);
+    const int NB = tile_nb3(L);
+    const int KW = NB + 2 * kPad;
+    const int N = L * NB;
+    p->nb = NB;
+    const size_t part_floats = (size_t)(KW / 4) * N * 4;
+    std::vector<float> ops(2 * part_floats, 0.0f);
+    for (int l = 0; l < L; ++l) {
+        const int a = line3_a(r, q.star, l), b = line3_b(r, q.star, l);
+        std::vector<double> band((size_t)KW * NB);
+        band_operand(r, q.cg + ((size_t)a * W + b) * W, NB, kPad, band.data());
+        for (int k = 0; k < KW; ++k)
+            for (int qq = 0; qq < NB; ++qq) {
+                const float h = (float)band[(size_t)k * NB + qq];
+                const float hi = tf32_round(h);
+                const size_t off = (size_t)(k / 4) * N * 4 + (size_t)(l * NB + qq) * 4 + (k % 4);
+                ops[off] = hi;
+                ops[part_floats + off] = tf32_round(h - hi);
+            }
+    }
+    p->n_lines = L;
+    p->n_scalar = 0;
+    p->operand_bytes = ops.size() * sizeof(float);
+    cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
+    if (e != cudaSuccess) {
+        if (why) *why = std::string("operand upload: ") + cudaGetErrorString(e);
+        return STENCIL_ENOMEM;
+    }
+    e = cudaMemcpy(p->d_operands, ops.data(), p->operand_bytes, cudaMemcpyHostToDevice);
+    Mx3State* st = new Mx3State();
+    st->nb = NB;
+    st->star = q.star;
+    st->bop_bytes = (uint32_t)p->operand_bytes;
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel3_for(r, q.star), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes_3d(KW, st->bop_bytes));
+    p->tmap_storage = st;
+    if (e != cudaSuccess) {
+        if (why) *why = std::string("3D plan set-up: ") + cudaGetErrorString(e);
+        mx3d_plan_free(p);
+        return STENCIL_ECUDA;
+    }
+    *st->err_host = 0;
+    return STENCIL_OK;
+}
+
+void mx3d_plan_free(MxPlan* p) {
+    if (p->d_operands) cudaFree(p->d_operands);
+    p->d_operands = nullptr;
+    Mx3State* st = (Mx3State*)p->tmap_storage;
+    if (st) {
+        if (st->err_host) cudaFreeHost(st->err_host);
+        delete st;
+    }
+    p->tmap_storage = nullptr;
+}
+
+unsigned int mx3d_device_error(const MxPlan& p) {
+    const Mx3State* st = (const Mx3State*)p.tmap_storage;
+    return st && st->err_host ? *(volatile unsigned int*)st->err_host : 0u;
+}
+
+cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s) {
+    if (tb != 1) return cudaErrorInvalidValue;
+    if (((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return cudaErrorMisalignedAddress;
+    const Mx3State* st = (const Mx3State*)p.tmap_storage;
+    const int nz = (int)p.n[0], ny = (int)p.n[1], nx = (int)p.n[2];
+    const int in_w = st->nb + 2 * kPad;
+    const int rows_tile = kQuarters * (kSlabRows - 2 * p.r);
+    MxArgs3D a;
+    memset(&a, 0, sizeof(a));
+    a.bops = (const float*)p.d_operands;
+    a.err = st->err_dev;
+    a.nz = nz;
+    a.ny = ny;
+    a.nx = nx;
+    a.nprod = (p.prec == STENCIL_PREC_TF32X3) ? 3 : 1;
+    a.tiles_x = (nx + st->nb - 1) / st->nb;
+    a.tiles_y = (ny + rows_tile - 1) / rows_tile;
+    a.chunks = (nz + kChunk - 1) / kChunk;
+    a.units = a.tiles_x * a.tiles_y * a.chunks;
+    a.bop_bytes = st->bop_bytes;
+    alignas(64) CUtensorMap map, map_out;
+    if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, in_w)) return cudaErrorInvalidValue;
+    if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb, rows_tile)) return cudaErrorInvalidValue;
+    const int grid = a.units < st->num_sms ? a.units : st->num_sms;
+    kernel3_for(p.r, st->star)<<<grid, kThreads, smem_bytes_3d(in_w, a.bop_bytes), s>>>(map, map_out, a);
+    return cudaGetLastError();
+}
+
+}  // namespace stx

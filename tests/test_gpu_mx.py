@@ -82,3 +82,37 @@ def test_mx_rejects_unaligned_rows():
     with pytest.raises(sx.StencilError) as ei:
         sx.stencil_plan_create((64, 66), 1, "box", np.ones((3, 3)) / 9, "f32", sx.make_options(impl="matrixized"))
     assert ei.value.status == sx.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("star", 3)])
+@pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
+def test_mx_3d(prec, kind, r, shape):
+    """3D matrixized sweep (plane streaming, lines along N) vs the oracle:
+    several y tiles, x tiles and z chunks plus ragged tails."""
+    if min(shape) < 2 * r + 1:
+        pytest.skip("below the minimum extent")
+    a, cg = problem(3, shape, r, kind, seed=40 + r)
+    steps = 3
+    got, info = run(a, r, kind, cg, "f32", "dirichlet", steps, impl="matrixized", prec=prec)
+    assert info["impl"] == 2 and info["device_error"] == 0
+    check(got, oracle.gather(a, r, cg, "dirichlet", steps), TOL[prec], f"mx 3d {kind} r={r} {shape} {prec}")
+
+
+def test_mx_3d_symmetric_closed_form():
+    """Symmetric 7-point star on a Dirichlet sine mode: lam^T times the mode."""
+    shape = (36, 40, 48)
+    cg = si.coeffs_symmetric_3d7p()
+    m = (1, 2, 1)
+    phi = [np.pi * mk / (nk + 1) for mk, nk in zip(m, shape)]
+    lam = sum(cg[o] * np.prod([np.cos(p * (oi - 1)) for p, oi in zip(phi, o)]) for o in np.ndindex(3, 3, 3))
+    xs = np.meshgrid(*[np.arange(s, dtype=np.float64) for s in shape], indexing="ij")
+    f = np.ones(shape)
+    for p, x in zip(phi, xs):
+        f = f * np.sin(p * (x + 1))
+    f = si.round_to(f, "f32")
+    T = 20
+    got, _ = run(f, 1, "star", cg, "f32", "dirichlet", T, impl="matrixized", prec="tf32x3")
+    check(got, oracle.gather(f, 1, cg, "dirichlet", T), 1e-5, "3d sine mode")
+    l2, _ = oracle.error_norms(got, lam ** T * f)
+    assert l2 < 1e-5
