@@ -200,14 +200,49 @@ STENCIL_API stencil_status stencil_wait(uint64_t ticket, int64_t timeout_ms);
 STENCIL_API const char *stencil_last_error(void);
 
 /* ---------------------------------------------------------------------------
- * Batches.  stencil_batch_run advances n independent problems, problem i by
- * steps[i] time steps from d_in[i] into d_out[i] (each with plans[i]), with
- * every sweep of every problem queued on `stream`.  Problems of equal
- * structure are packed into shared persistent launches.  Errors as for
- * stencil_apply, reported for the first failing problem.
+ * Batches: many independent problems advanced together (problem i by steps[i]
+ * time steps from d_in[i] into d_out[i], with plans[i]).  When every plan is
+ * 2D with the same order, kind and dtype (order <= 3), all problems are packed
+ * into shared persistent launches: launch k advances every problem that still
+ * has steps left by up to `tb` steps (temporal blocking), each with its own
+ * coefficients and boundary.  Otherwise each problem runs its own sweeps.  In
+ * both cases the whole launch sequence is captured once in a CUDA graph and
+ * replayed by stencil_batch_launch.
+ *
+ * stencil_batch_create -- build the schedule and the graph.
+ *   tb  time steps per launch; 0 = autotune: each depth 1..4 that fits shared
+ *       memory is timed on one launch of this batch (reading d_in, writing the
+ *       plans' scratch grids) and the fastest per step is kept (cached per
+ *       order, kind, dtype and batch size class).  d_in must hold the inputs
+ *       when create is called if tb = 0.
+ *   The arrays plans/d_in/d_out/steps are copied; the buffers must stay valid
+ *   while the batch exists.  d_in[i] == d_out[i] is allowed.
+ * Errors: EINVAL (NULL or negative entries), EUNSUPPORTED (tb too deep for
+ * shared memory), ENOMEM / ECUDA.
  */
+typedef struct stencil_batch_s *stencil_batch_t;
+
+typedef struct {
+    int32_t packed;    /* 1: problems share persistent launches                */
+    int32_t tb;        /* time steps per launch                                */
+    int32_t launches;  /* packed launches per run (-1 when not packed)         */
+    int32_t reserved;
+    int64_t tiles;     /* output tiles processed per run (packed)              */
+    int64_t updates;   /* stencil updates per run (sum of points x steps)      */
+} stencil_batch_info_t;
+
+STENCIL_API stencil_status stencil_batch_create(stencil_batch_t *out, int n, const stencil_plan_t *plans,
+                                                const void *const *d_in, void *const *d_out, const int64_t *steps,
+                                                int32_t tb);
+/* Queue one run of the batch (one graph launch) on `stream`; asynchronous. */
+STENCIL_API stencil_status stencil_batch_launch(stencil_batch_t batch, stencil_stream_t stream);
+STENCIL_API stencil_status stencil_batch_info(stencil_batch_t batch, stencil_batch_info_t *info);
+/* Free the batch after its queued runs have finished.  NULL is accepted. */
+STENCIL_API stencil_status stencil_batch_destroy(stencil_batch_t batch);
+
+/* One-shot: create (autotuned), launch on `stream`, wait for it, destroy. */
 STENCIL_API stencil_status stencil_batch_run(int n, const stencil_plan_t *plans, const void *const *d_in,
-                                 void *const *d_out, const int64_t *steps, stencil_stream_t stream);
+                                             void *const *d_out, const int64_t *steps, stencil_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Error norms against a reference (the accuracy report attached to every

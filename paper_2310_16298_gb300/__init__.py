@@ -50,6 +50,11 @@ class stencil_options(ctypes.Structure):
                 ("tb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
+class stencil_batch_info_t(ctypes.Structure):
+    _fields_ = [("packed", ctypes.c_int32), ("tb", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tiles", ctypes.c_int64), ("updates", ctypes.c_int64)]
+
+
 class stencil_plan_info_t(ctypes.Structure):
     _fields_ = [("impl", ctypes.c_int32), ("prec", ctypes.c_int32), ("tb", ctypes.c_int32),
                 ("n_lines", ctypes.c_int32), ("n_scalar", ctypes.c_int32), ("tile_n", ctypes.c_int32),
@@ -77,6 +82,11 @@ _SIGS = {
     "stencil_last_error": (ctypes.c_char_p, []),
     "stencil_batch_run": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), _I64P, _P]),
+    "stencil_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                            ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.c_int32]),
+    "stencil_batch_launch": (ctypes.c_int, [_P, _P]),
+    "stencil_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(stencil_batch_info_t)]),
+    "stencil_batch_destroy": (ctypes.c_int, [_P]),
     "stencil_error_norms": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _DP, _P]),
     "stencil_band_operand": (ctypes.c_int, [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, _DP]),
     "stencil_line_cover": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -197,6 +207,33 @@ def stencil_batch_run(plans: Sequence[int], d_in: Sequence[int], d_out: Sequence
     O = (_P * n)(*d_out)
     S = np.ascontiguousarray(steps, dtype=np.int64)
     _check(lib().stencil_batch_run(n, P, I, O, S.ctypes.data_as(_I64P), stream), "stencil_batch_run")
+
+
+def stencil_batch_create(plans: Sequence[int], d_in: Sequence[int], d_out: Sequence[int],
+                         steps: Sequence[int], tb: int = 0) -> int:
+    n = len(plans)
+    h = _P()
+    P = (_P * n)(*plans)
+    I = (_P * n)(*d_in)
+    O = (_P * n)(*d_out)
+    S = np.ascontiguousarray(steps, dtype=np.int64)
+    _check(lib().stencil_batch_create(ctypes.byref(h), n, P, I, O, S.ctypes.data_as(_I64P), int(tb)),
+           "stencil_batch_create")
+    return h.value
+
+
+def stencil_batch_launch(batch: int, stream: int = 0):
+    _check(lib().stencil_batch_launch(batch, stream), "stencil_batch_launch")
+
+
+def stencil_batch_info(batch: int) -> dict:
+    info = stencil_batch_info_t()
+    _check(lib().stencil_batch_info(batch, ctypes.byref(info)), "stencil_batch_info")
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def stencil_batch_destroy(batch: int):
+    _check(lib().stencil_batch_destroy(batch), "stencil_batch_destroy")
 
 
 def stencil_error_norms(d_got: int, got_dtype, d_ref: int, count: int, stream: int = 0) -> np.ndarray:

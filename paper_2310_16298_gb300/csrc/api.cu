@@ -18,29 +18,11 @@
 #include "kernels.h"
 #include "mx.h"
 #include "plan.h"
+#include "runtime.h"
 
 using namespace stx;
 
-struct stencil_plan_s {
-    int ndim = 0;
-    int64_t n[3] = {1, 1, 1};
-    int r = 0;
-    bool star = false;
-    bool f64 = false;
-    int bc = kBcDirichlet;
-    std::vector<double> cg;
-    int impl = STENCIL_IMPL_GATHER;
-    int prec = STENCIL_PREC_NATIVE;
-    int tb = 1;
-    int device = 0;
-    int64_t points = 0;
-    size_t grid_bytes = 0;
-    void* scratch = nullptr;
-    cudaStream_t stream = nullptr;  // for stencil_submit
-    MxPlan* mx = nullptr;
-};
-
-namespace {
+namespace stx {
 
 thread_local std::string g_err;
 
@@ -53,6 +35,8 @@ stencil_status cuda_fail(cudaError_t e, const char* what) {
     g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return STENCIL_ECUDA;
 }
+
+const std::string& last_error_string() { return g_err; }
 
 GatherProblem gather_problem(const stencil_plan_s* p) {
     GatherProblem g;
@@ -103,6 +87,10 @@ stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out,
     }
     return STENCIL_OK;
 }
+
+}  // namespace stx
+
+namespace {
 
 // ----------------------------------------------------------------- tickets
 std::mutex g_tk_mu;
@@ -430,24 +418,6 @@ extern "C" stencil_status stencil_wait(uint64_t ticket, int64_t timeout_ms) {
 }
 
 extern "C" const char* stencil_last_error(void) { return g_err.c_str(); }
-
-// =================================================================== batches
-extern "C" stencil_status stencil_batch_run(int n, const stencil_plan_t* plans, const void* const* d_in,
-                                            void* const* d_out, const int64_t* steps,
-                                            stencil_stream_t stream) {
-    if (n < 0) return fail(STENCIL_EINVAL, "n must be >= 0");
-    if (n == 0) return STENCIL_OK;
-    if (!plans || !d_in || !d_out || !steps) return fail(STENCIL_EINVAL, "NULL argument");
-    for (int i = 0; i < n; ++i)
-        if (!plans[i] || !d_in[i] || !d_out[i] || steps[i] < 0)
-            return fail(STENCIL_EINVAL, "invalid entry " + std::to_string(i));
-    for (int i = 0; i < n; ++i) {
-        stencil_status st = time_loop(plans[i], d_in[i], d_out[i], steps[i], (cudaStream_t)stream,
-                                      plans[i]->scratch);
-        if (st != STENCIL_OK) return fail(st, "problem " + std::to_string(i) + ": " + g_err);
-    }
-    return STENCIL_OK;
-}
 
 // =================================================================== norms
 extern "C" stencil_status stencil_error_norms(const void* d_got, stencil_dtype got_dtype, const double* d_ref,

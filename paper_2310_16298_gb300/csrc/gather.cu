@@ -57,13 +57,13 @@ __device__ __forceinline__ const T* src3(const T* __restrict__ a, int64_t z, int
 // ---------------------------------------------------------------------------
 // 2D.  Block = (32, BY) threads; output tile TY x TX.  Strips run along y.
 // ---------------------------------------------------------------------------
+// One output tile (origin y0, x0) advanced by tb steps; shared by the
+// single-problem and the batched kernels.
 template <typename T, int R, bool STAR, int BY, int TX, int TY>
-__global__ void __launch_bounds__(kBX * BY)
-gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64_t nx, int bc,
-                int tb, Coeffs<T, ipow(2 * R + 1, 2)> cf) {
+__device__ __forceinline__ void gather2d_tile(const T* __restrict__ in, T* __restrict__ out, int64_t ny,
+                                              int64_t nx, int bc, int tb, const Coeffs<T, ipow(2 * R + 1, 2)>& cf,
+                                              int64_t y0, int64_t x0, T* smem) {
     constexpr int W = 2 * R + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* smem = reinterpret_cast<T*>(smem_raw);
     const int H = R * tb;
     const int SX = TX + 2 * H;
     const int SY = TY + 2 * H;
@@ -71,7 +71,6 @@ gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64
     T* buf[2] = {smem, smem + SY * SX};
     const int rows_alloc = (tb > 1 ? 2 * SY : SY) + kRS;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t y0 = (int64_t)blockIdx.y * TY, x0 = (int64_t)blockIdx.x * TX;
 
     const bool interior = (y0 - H >= 0) && (y0 + TY + H <= ny) && (x0 - H >= 0) && (x0 + TX + H <= nx);
     for (int sy = ty; sy < rows_alloc; sy += BY) {
@@ -136,6 +135,42 @@ gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64
             }
         }
         __syncthreads();
+    }
+}
+
+template <typename T, int R, bool STAR, int BY, int TX, int TY>
+__global__ void __launch_bounds__(kBX * BY)
+gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64_t nx, int bc,
+                int tb, Coeffs<T, ipow(2 * R + 1, 2)> cf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gather2d_tile<T, R, STAR, BY, TX, TY>(in, out, ny, nx, bc, tb, cf, (int64_t)blockIdx.y * TY,
+                                          (int64_t)blockIdx.x * TX, reinterpret_cast<T*>(smem_raw));
+}
+
+// Persistent batched sweep: the tiles of many independent problems, each
+// advanced by its own depth, processed by one grid-stride launch.  Problem
+// p owns tiles [tile0[p], tile0[p+1]); its coefficients sit at coef + p*NC.
+template <typename T, int R, bool STAR, int BY, int TX, int TY>
+__global__ void __launch_bounds__(kBX * BY)
+gather2d_batch_kernel(const BatchProblem* __restrict__ probs, int nprob, int total_tiles,
+                      const T* __restrict__ coef) {
+    constexpr int NC = ipow(2 * R + 1, 2);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        int lo = 0, hi = nprob - 1;  // last problem whose first tile <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchProblem P = probs[lo];
+        const int local = t - P.tile0;
+        Coeffs<T, NC> cf;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) cf.c[i] = coef[(size_t)P.coef_index * NC + i];
+        gather2d_tile<T, R, STAR, BY, TX, TY>((const T*)P.src, (T*)P.dst, P.ny, P.nx, P.bc, P.depth, cf,
+                                              (int64_t)(local / P.tiles_x) * TY, (int64_t)(local % P.tiles_x) * TX,
+                                              reinterpret_cast<T*>(smem_raw));
     }
 }
 
@@ -300,7 +335,51 @@ cudaError_t dispatch_r(const GatherProblem& p, const void* in, void* out, int tb
     return cudaErrorInvalidValue;
 }
 
+template <typename T, int R, bool STAR>
+cudaError_t launch_batch(const BatchProblem* probs, int nprob, int total_tiles, const void* coef, int max_tb,
+                         int grid, cudaStream_t s) {
+    const size_t smem = gather_smem_bytes_t<T>(2, R, max_tb);
+    auto kern = gather2d_batch_kernel<T, R, STAR, k2BY, k2TX, k2TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBX * k2BY, smem);
+        grid = sms * (per > 0 ? per : 1);
+    }
+    if (grid > total_tiles) grid = total_tiles;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, dim3(kBX, k2BY), smem, s>>>(probs, nprob, total_tiles, (const T*)coef);
+    return cudaGetLastError();
+}
+
+template <typename T, bool STAR>
+cudaError_t dispatch_batch(int r, const BatchProblem* probs, int nprob, int total_tiles, const void* coef,
+                           int max_tb, int grid, cudaStream_t s) {
+    switch (r) {
+        case 1: return launch_batch<T, 1, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+        case 2: return launch_batch<T, 2, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+        case 3: return launch_batch<T, 3, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+cudaError_t gather_batch_sweep(bool f64, bool star, int r, const BatchProblem* d_probs, int nprob, int total_tiles,
+                               const void* d_coef, int max_tb, cudaStream_t s) {
+    if (f64) return star ? dispatch_batch<double, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s)
+                         : dispatch_batch<double, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s);
+    return star ? dispatch_batch<float, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s)
+                : dispatch_batch<float, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s);
+}
+
+void gather_tile_shape(int ndim, int* ty, int* tx) {
+    *ty = ndim == 2 ? k2TY : k3TY;
+    *tx = ndim == 2 ? k2TX : k3TX;
+}
 
 size_t gather_smem_bytes(const GatherProblem& p, int tb) {
     return p.f64 ? gather_smem_bytes_t<double>(p.ndim, p.r, tb) : gather_smem_bytes_t<float>(p.ndim, p.r, tb);

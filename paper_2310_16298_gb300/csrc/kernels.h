@@ -22,6 +22,26 @@ struct GatherProblem {
 cudaError_t gather_sweep(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s);
 size_t gather_smem_bytes(const GatherProblem& p, int tb);
 
+// One problem of a batched launch (2D).
+struct BatchProblem {
+    const void* src;  // input grid of this launch
+    void* dst;        // output grid of this launch
+    int ny, nx;       // interior extents
+    int depth;        // time steps this launch advances the problem (>= 1)
+    int bc;           // kBcDirichlet | kBcPeriodic
+    int tiles_x;      // output tiles along x
+    int tile0;        // index of the problem's first tile in the launch
+    int coef_index;   // row of the coefficient table
+    int pad;
+};
+
+// Advance every listed problem by its depth in one persistent launch.
+// d_probs: device array sorted by tile0; d_coef: (2r+1)^2 entries per row.
+cudaError_t gather_batch_sweep(bool f64, bool star, int r, const BatchProblem* d_probs, int nprob, int total_tiles,
+                               const void* d_coef, int max_tb, cudaStream_t s);
+// Output tile of the 2D/3D gather kernels (rows, columns).
+void gather_tile_shape(int ndim, int* ty, int* tx);
+
 // FP64 error norms: out4 (device) = {sum d^2, sum ref^2, max|d|, max|ref|}.
 // `partials` is device scratch of norms_partials_bytes() bytes.
 size_t norms_partials_bytes();

@@ -1,0 +1,50 @@
+// Internal runtime structures shared by the host-side translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "mx.h"
+
+// A plan (opaque to callers): the validated problem, the chosen kernel and
+// the device memory the plan owns.
+struct stencil_plan_s {
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    int r = 0;
+    bool star = false;
+    bool f64 = false;
+    int bc = stx::kBcDirichlet;
+    std::vector<double> cg;
+    int impl = STENCIL_IMPL_GATHER;
+    int prec = STENCIL_PREC_NATIVE;
+    int tb = 1;
+    int device = 0;
+    int64_t points = 0;
+    size_t grid_bytes = 0;
+    void* scratch = nullptr;
+    cudaStream_t stream = nullptr;  // for stencil_submit
+    stx::MxPlan* mx = nullptr;
+};
+
+
+namespace stx {
+
+// Record a failure message for stencil_last_error() and return `st`.
+stencil_status fail(stencil_status st, const std::string& msg);
+stencil_status cuda_fail(cudaError_t e, const char* what);
+const std::string& last_error_string();
+
+GatherProblem gather_problem(const stencil_plan_s* p);
+cudaError_t run_sweep(const stencil_plan_s* p, const void* src, void* dst, int tb, cudaStream_t s);
+// Advance d_in by `steps` into d_out on stream s, ping-ponging through `scratch`.
+stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out, int64_t steps, cudaStream_t s,
+                         void* scratch);
+
+}  // namespace stx
