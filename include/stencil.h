@@ -245,6 +245,70 @@ STENCIL_API stencil_status stencil_batch_run(int n, const stencil_plan_t *plans,
                                              void *const *d_out, const int64_t *steps, stencil_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of stencil solves.
+ *
+ * A server owns a worker thread.  Submitted requests are admitted in arrival
+ * order while the device-memory budget (each request is charged three grids
+ * plus 1 MiB: two copies and its plan's scratch grid) and the resident-slot
+ * limit allow.  Every resident request advances by at most `quantum_steps`
+ * time steps per issue on one of `nstreams` streams, so requests overlap on
+ * the device and new ones join as soon as memory and a slot free up.  A
+ * finished grid is copied to host memory and the request's device state is
+ * freed.  Each request runs through the same plan and kernels as
+ * stencil_apply, so its result is the same alone and in any mix.
+ */
+typedef struct stencil_server_s *stencil_server_t;
+
+typedef struct {
+    int32_t ndim, radius, kind, dtype, bc, impl;  /* as for stencil_plan_create / stencil_options */
+    int64_t shape[3];                             /* ndim interior extents                        */
+    const double *coeffs;  /* dense C^g; copied by submit                                              */
+    const void *h_in;      /* host input grid (dtype, C order), read at admission; keep it valid
+                              until the request finishes.  NULL: the input is the uniform[lo, hi)
+                              SplitMix64 field of `seed` (element i of the seed's stream in C order),
+                              generated on the device                                              */
+    uint64_t seed;
+    double lo, hi;
+    int64_t steps;         /* time steps to advance, >= 0                                          */
+} stencil_request;
+
+typedef struct {
+    double submit_s, admit_s, done_s;  /* seconds since the server was created                 */
+    int32_t impl;                      /* stencil_impl that ran                                 */
+    int32_t status;                    /* stencil_status of the request                         */
+    int64_t updates;                   /* points x steps                                        */
+} stencil_request_stats;
+
+typedef struct {
+    int64_t queued, resident, admitted, completed;
+    int64_t bytes_in_use, peak_bytes, peak_resident, quanta_issued;
+} stencil_server_stats_t;
+
+/* budget_bytes > 0, max_resident >= 1, quantum_steps >= 1, 1 <= nstreams <= 64. */
+STENCIL_API stencil_status stencil_server_create(stencil_server_t *out, int64_t budget_bytes, int32_t max_resident,
+                                                 int32_t quantum_steps, int32_t nstreams);
+/* Queue a request; *id identifies it.  EINVAL for an invalid problem, ENOMEM
+ * when one request alone exceeds the budget. */
+STENCIL_API stencil_status stencil_server_submit(stencil_server_t server, const stencil_request *request,
+                                                 uint64_t *id);
+/* OK once the request finished, ENOTREADY before, its error if it failed. */
+STENCIL_API stencil_status stencil_server_poll(stencil_server_t server, uint64_t id);
+/* Block up to timeout_ms (< 0: no limit); ETIMEDOUT leaves the request running. */
+STENCIL_API stencil_status stencil_server_wait(stencil_server_t server, uint64_t id, int64_t timeout_ms);
+/* Copy a finished result to h_out (NULL: discard), fill stats, release the id. */
+STENCIL_API stencil_status stencil_server_result(stencil_server_t server, uint64_t id, void *h_out,
+                                                 stencil_request_stats *stats);
+STENCIL_API stencil_status stencil_server_stats(stencil_server_t server, stencil_server_stats_t *stats);
+/* Finish every submitted request, then stop the worker and free the server. */
+STENCIL_API stencil_status stencil_server_destroy(stencil_server_t server);
+
+/* Fill a device array with the uniform[lo, hi) SplitMix64 field of `seed`
+ * (elements offset .. offset+count-1 of the stream, rounded to dtype); the
+ * same values the seeded host generator gives.  Asynchronous on stream. */
+STENCIL_API stencil_status stencil_fill_uniform(void *d_out, stencil_dtype dtype, int64_t count, uint64_t seed,
+                                                int64_t offset, double lo, double hi, stencil_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Error norms against a reference (the accuracy report attached to every
  * result).  Computes, in FP64 on the device,
  *   out[0] = sum (got - ref)^2,  out[1] = sum ref^2,

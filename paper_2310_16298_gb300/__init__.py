@@ -55,6 +55,24 @@ class stencil_batch_info_t(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("tiles", ctypes.c_int64), ("updates", ctypes.c_int64)]
 
 
+class stencil_request(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("radius", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("bc", ctypes.c_int32), ("impl", ctypes.c_int32),
+                ("shape", ctypes.c_int64 * 3), ("coeffs", ctypes.POINTER(ctypes.c_double)),
+                ("h_in", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("lo", ctypes.c_double),
+                ("hi", ctypes.c_double), ("steps", ctypes.c_int64)]
+
+
+class stencil_request_stats(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("impl", ctypes.c_int32), ("status", ctypes.c_int32), ("updates", ctypes.c_int64)]
+
+
+class stencil_server_stats_t(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("queued", "resident", "admitted", "completed", "bytes_in_use",
+                                              "peak_bytes", "peak_resident", "quanta_issued")]
+
+
 class stencil_plan_info_t(ctypes.Structure):
     _fields_ = [("impl", ctypes.c_int32), ("prec", ctypes.c_int32), ("tb", ctypes.c_int32),
                 ("n_lines", ctypes.c_int32), ("n_scalar", ctypes.c_int32), ("tile_n", ctypes.c_int32),
@@ -87,6 +105,16 @@ _SIGS = {
     "stencil_batch_launch": (ctypes.c_int, [_P, _P]),
     "stencil_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(stencil_batch_info_t)]),
     "stencil_batch_destroy": (ctypes.c_int, [_P]),
+    "stencil_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32]),
+    "stencil_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(stencil_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "stencil_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "stencil_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64]),
+    "stencil_server_result": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(stencil_request_stats)]),
+    "stencil_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(stencil_server_stats_t)]),
+    "stencil_server_destroy": (ctypes.c_int, [_P]),
+    "stencil_fill_uniform": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
+                                            ctypes.c_double, ctypes.c_double, _P]),
     "stencil_error_norms": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _DP, _P]),
     "stencil_band_operand": (ctypes.c_int, [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, _DP]),
     "stencil_line_cover": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -234,6 +262,74 @@ def stencil_batch_info(batch: int) -> dict:
 
 def stencil_batch_destroy(batch: int):
     _check(lib().stencil_batch_destroy(batch), "stencil_batch_destroy")
+
+
+def stencil_fill_uniform(d_out: int, dtype, count: int, seed: int, offset: int = 0, lo: float = 0.0,
+                         hi: float = 1.0, stream: int = 0):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().stencil_fill_uniform(d_out, dt, int(count), int(seed) & 0xFFFFFFFFFFFFFFFF, int(offset),
+                                      float(lo), float(hi), stream), "stencil_fill_uniform")
+
+
+def stencil_server_create(budget_bytes: int, max_resident: int = 64, quantum_steps: int = 16,
+                          nstreams: int = 8) -> int:
+    h = _P()
+    _check(lib().stencil_server_create(ctypes.byref(h), int(budget_bytes), int(max_resident), int(quantum_steps),
+                                       int(nstreams)), "stencil_server_create")
+    return h.value
+
+
+def make_request(shape, radius, kind, coeffs, dtype, steps, bc="dirichlet", impl="auto", h_in=None,
+                 seed=0, lo=0.0, hi=1.0):
+    """A stencil_request plus the Python objects its pointers refer to (keep both alive)."""
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    rq = stencil_request()
+    rq.ndim = len(shape)
+    rq.radius = int(radius)
+    rq.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+    rq.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    rq.bc = BCS[bc] if isinstance(bc, str) else int(bc)
+    rq.impl = IMPLS[impl] if isinstance(impl, str) else int(impl)
+    for d, n in enumerate(shape):
+        rq.shape[d] = int(n)
+    rq.coeffs = _dp(c)
+    rq.h_in = h_in.ctypes.data if h_in is not None else None
+    rq.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    rq.lo = float(lo)
+    rq.hi = float(hi)
+    rq.steps = int(steps)
+    return rq, (c, h_in)
+
+
+def stencil_server_submit(server: int, rq: stencil_request) -> int:
+    i = ctypes.c_uint64()
+    _check(lib().stencil_server_submit(server, ctypes.byref(rq), ctypes.byref(i)), "stencil_server_submit")
+    return i.value
+
+
+def stencil_server_poll(server: int, rid: int) -> int:
+    return int(lib().stencil_server_poll(server, rid))
+
+
+def stencil_server_wait(server: int, rid: int, timeout_ms: int = -1) -> int:
+    return int(lib().stencil_server_wait(server, rid, int(timeout_ms)))
+
+
+def stencil_server_result(server: int, rid: int, h_out: Optional[np.ndarray] = None) -> dict:
+    st = stencil_request_stats()
+    _check(lib().stencil_server_result(server, rid, h_out.ctypes.data if h_out is not None else None,
+                                       ctypes.byref(st)), "stencil_server_result")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def stencil_server_stats(server: int) -> dict:
+    st = stencil_server_stats_t()
+    _check(lib().stencil_server_stats(server, ctypes.byref(st)), "stencil_server_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def stencil_server_destroy(server: int):
+    _check(lib().stencil_server_destroy(server), "stencil_server_destroy")
 
 
 def stencil_error_norms(d_got: int, got_dtype, d_ref: int, count: int, stream: int = 0) -> np.ndarray:

@@ -440,6 +440,17 @@ extern "C" stencil_status stencil_error_norms(const void* d_got, stencil_dtype g
     return STENCIL_OK;
 }
 
+// =================================================================== synthetic fields
+extern "C" stencil_status stencil_fill_uniform(void* d_out, stencil_dtype dtype, int64_t count, uint64_t seed,
+                                               int64_t offset, double lo, double hi, stencil_stream_t stream) {
+    if (!d_out && count > 0) return fail(STENCIL_EINVAL, "NULL argument");
+    if (count < 0 || offset < 0) return fail(STENCIL_EINVAL, "count and offset must be >= 0");
+    if (dtype != STENCIL_F32 && dtype != STENCIL_F64) return fail(STENCIL_EINVAL, "bad dtype");
+    cudaError_t e = fill_uniform(d_out, dtype == STENCIL_F64, count, seed, offset, lo, hi, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fill launch");
+    return STENCIL_OK;
+}
+
 // =================================================================== host algebra
 extern "C" stencil_status stencil_band_operand(int radius, const double* line, int n, int pad, double* band) {
     if (!line || !band) return fail(STENCIL_EINVAL, "NULL argument");

@@ -42,6 +42,11 @@ cudaError_t gather_batch_sweep(bool f64, bool star, int r, const BatchProblem* d
 // Output tile of the 2D/3D gather kernels (rows, columns).
 void gather_tile_shape(int ndim, int* ty, int* tx);
 
+// Uniform[lo, hi) SplitMix64 field (elements offset .. offset+count-1 of the
+// seed's stream), rounded to the storage type.
+cudaError_t fill_uniform(void* out, bool f64, int64_t count, uint64_t seed, int64_t offset, double lo, double hi,
+                         cudaStream_t s);
+
 // FP64 error norms: out4 (device) = {sum d^2, sum ref^2, max|d|, max|ref|}.
 // `partials` is device scratch of norms_partials_bytes() bytes.
 size_t norms_partials_bytes();
