@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
-                    choices=["box25-8192", "star7-512", "box27-512", "jacobi-256", "batch-1024"])
+                    choices=["box25-8192", "star7-512", "box27-512", "jacobi-256", "batch-1024", "serve-2000"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
@@ -310,6 +310,78 @@ def run_batch_workload(args):
         sx.stencil_plan_destroy(p)
 
 
+# ------------------------------------------------------------------ serving workload
+def run_serving_workload(args):
+    """Poisson arrivals of mixed stencil solves (70% 2D 128^2..4096^2 r=1..3
+    star|box, 30% 3D 64^3..384^3 7/27-point, 10% FP64, steps 10..500) served
+    with continuous batching under a 120 GB budget.  The saturated rate is
+    measured first (all requests queued at once); then the same requests
+    arrive as Poisson streams at 0.5x and 0.8x that rate and the latency
+    (arrival to result on the host) is reported."""
+    rank, world, local = dist_env()
+    import torch
+    import paper_2310_16298_gb300 as sx
+    import stencil_inputs as si
+    torch.cuda.set_device(local)
+    n = args.batch if args.batch != 1024 else 2000
+    base = si.serving_stream(n, rate_per_s=1.0)
+
+    def serve(arrivals):
+        srv = sx.stencil_server_create(120 * 10**9, 64, 16, 8)
+        keep, ids = [], []
+        t0 = time.perf_counter()
+        for (t_arr, rq) in arrivals:
+            dt = t0 + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            p = rq.problem
+            r, ref = sx.make_request(p.shape, p.r, p.kind, p.coeffs, p.dtype, p.steps, bc=p.bc,
+                                     seed=p.field_seed, lo=p.field_lo, hi=p.field_hi)
+            keep.append((r, ref))
+            ids.append(sx.stencil_server_submit(srv, r))
+        lat, upd, first, last = [], 0, None, 0.0
+        for rid in ids:
+            assert sx.stencil_server_wait(srv, rid, -1) == sx.OK, sx.stencil_last_error()
+            st = sx.stencil_server_result(srv, rid, None)
+            lat.append(st["done_s"] - st["submit_s"])
+            upd += st["updates"]
+            first = st["submit_s"] if first is None else min(first, st["submit_s"])
+            last = max(last, st["done_s"])
+        stats = sx.stencil_server_stats(srv)
+        sx.stencil_server_destroy(srv)
+        return np.array(lat), upd, last - first, stats
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    lat_s, upd, span, st_s = serve([(0.0, q) for q in base])
+    sat_rate = n / span
+    results = {"saturated": {"requests_per_s": sat_rate, "gstencil_s": upd / span / 1e9, "makespan_s": span,
+                             "p50_latency_s": float(np.percentile(lat_s, 50)),
+                             "p99_latency_s": float(np.percentile(lat_s, 99)), "peak_resident": st_s["peak_resident"],
+                             "peak_bytes": st_s["peak_bytes"]}}
+    for frac in (0.5, 0.8):
+        stream = si.serving_stream(n, rate_per_s=frac * sat_rate)
+        lat, upd_f, span_f, st_f = serve([(q.arrival_s, q) for q in stream])
+        results[f"load_{frac}"] = {"offered_requests_per_s": frac * sat_rate, "gstencil_s": upd_f / span_f / 1e9,
+                                   "p50_latency_s": float(np.percentile(lat, 50)),
+                                   "p99_latency_s": float(np.percentile(lat, 99)),
+                                   "peak_resident": st_f["peak_resident"], "peak_bytes": st_f["peak_bytes"]}
+    clk = sampler.stop()
+    if rank == 0:
+        head = results["load_0.8"]
+        line = {"metric": METRIC, "value": head["gstencil_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
+                "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"serving: {n} Poisson-arrival requests, 70% 2D (128^2..4096^2, r 1..3, "
+                                       f"star|box), 30% 3D (64^3..384^3, 7/27-point), FP32 with 10% FP64, steps "
+                                       f"10..500, 120 GB admission budget, 64 slots, quantum 16 steps",
+                           "value_is": "GStencil/s over the makespan at offered load 0.8 x saturated rate",
+                           "parallelism": f"replicas x{world}"},
+                "p50_ms": head["p50_latency_s"] * 1e3, "p99_ms": head["p99_latency_s"] * 1e3,
+                "serving": results, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -317,6 +389,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch-1024":
         return run_batch_workload(args)
+    if args.workload == "serve-2000":
+        return run_serving_workload(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_16298_gb300 as sx
