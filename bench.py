@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
     ap.add_argument("--dtype", default="", choices=["", "f32", "f64"], help="storage type ('' = the workload's own)")
+    ap.add_argument("--prec", default="native", choices=["native", "tf32", "tf32x3", "bf16", "bf16x2", "bf16x3"],
+                    help="matrixized arithmetic (native = TF32x3 for FP32)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -416,7 +418,8 @@ def main():
     results = {}
     for impl in ("matrixized", "gather"):
         try:
-            plan = sx.Plan(p.shape, p.r, p.kind, p.coeffs, p.dtype, bc=p.bc, impl=impl)
+            plan = sx.Plan(p.shape, p.r, p.kind, p.coeffs, p.dtype, bc=p.bc, impl=impl,
+                           prec=args.prec if impl == "matrixized" else "native")
         except sx.StencilError as e:
             results[impl] = {"unavailable": str(e)}
             continue

@@ -59,19 +59,26 @@ constexpr int kRawStages = 6;           // TMA ring depth
 constexpr int kTmemCols = 512;
 
 // Output columns per tile (the MMA block width) for a stencil with L lines:
-// 32 while both accumulator sets (2 x L x 32 columns) and both A stages
-// (2 x 2 x 40 columns) fit the 512 TMEM columns, else 16.
-__host__ __device__ constexpr int tile_nb(int L) { return (2 * L * 32 + 4 * (32 + 2 * kPad) <= kTmemCols) ? 32 : 16; }
+// 32 while both accumulator sets (2 x L x 32 columns) and both A stages fit
+// the 512 TMEM columns, else 16.
+template <bool BF>
+__host__ __device__ constexpr int a_stage_cols(int nb) {
+    return OpFmt<BF>::kMaxParts * OpFmt<BF>::part_cols(OpFmt<BF>::window(nb));
+}
+template <bool BF>
+__host__ __device__ constexpr int tile_nb(int L) { return (2 * L * 32 + 2 * a_stage_cols<BF>(32) <= kTmemCols) ? 32 : 16; }
 
 struct MxArgs2D {
     float* out;
     const float* in;          // source grid (periodic halo fix-up reads it directly)
-    const float* bops;        // banded operands [part][kchunk][line*NB + q][4]
+    const void* bops;         // banded operands [part][kchunk][line*NB + q][16 bytes]
     unsigned int* err;        // device error word (host-mapped)
     int ny, nx;
-    int bc, nprod;             // nprod: 1 (TF32) or 3 (TF32x3)
+    int bc, nparts;            // operand parts of the input split (1..3)
     int tiles_x, tiles_total;
-    uint32_t bop_bytes;        // both parts
+    uint32_t bop_bytes;        // every part
+    uint32_t bpart_bytes;      // one part
+    Products prods;            // (A part, B part) products, smallest first
 };
 
 __host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
@@ -80,8 +87,8 @@ __host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters *
 // floats, each stage padded to 1 KB (the swizzle span).
 __host__ __device__ constexpr int out_stage_bytes(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
 
-size_t smem_bytes_2d(int in_w, uint32_t bop_bytes) {
-    return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + 2 * (size_t)out_stage_bytes(in_w - 8) +
+size_t smem_bytes_2d(int nb, int in_w, uint32_t bop_bytes) {
+    return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + 2 * (size_t)out_stage_bytes(nb) +
            bop_bytes + 8 * (2 * kRawStages + 16);
 }
 
@@ -105,18 +112,21 @@ size_t smem_bytes_2d(int in_w, uint32_t bop_bytes) {
 //    only (NB+8)/8 large additions (the tensor core's FP32 accumulation
 //    truncates); the lines are summed in FP32 round-to-nearest in the
 //    epilogue.
-template <int R, int NB>
+template <int R, int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
             const MxArgs2D args) {
+    using F = OpFmt<BF>;
     constexpr int L = 2 * R + 1;            // lines
     constexpr int N = L * NB;               // MMA N
-    constexpr int K = NB + 2 * kPad;        // input columns per tile = K window
-    constexpr int KS = K / 8;               // tf32 MMAs per window
+    constexpr int K = F::window(NB);        // input columns per tile = K window
+    constexpr int KS = K / F::kKStep;       // MMAs per window and product
     constexpr int ROWS_OUT = kSlabRows - 2 * R;
-    constexpr int A_COLS = 2 * K;           // TMEM columns of one A stage (hi | lo)
+    constexpr int PC = F::part_cols(K);     // TMEM columns of one operand part
+    constexpr int A_COLS = F::kMaxParts * PC;  // TMEM columns of one A stage
     constexpr int CW = NB / kSubs;          // epilogue columns per epilogue warp
-    constexpr int NG = K / 8;               // 8-column groups of the input tile
+    constexpr int GW = F::kGroup;           // input columns per split group
+    constexpr int NG = K / GW;              // split groups of the input tile
     constexpr int RSB = raw_stage_bytes(K);
     constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
@@ -195,10 +205,9 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
-            constexpr uint32_t idesc = ptx::instr_desc(2, 2, 128, (uint32_t)N);
-            const uint32_t part_bytes = args.bop_bytes / 2;
-            const uint64_t bhi0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
-            const uint64_t blo0 = bhi0 + (uint64_t)(part_bytes >> 4);
+            constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
+            const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
+            const Products pr = args.prods;
             int i = 0;
             for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
                 const int st = i & 1;
@@ -206,21 +215,8 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 if (!wait_or_abort(&afull[st], ph, abort_flag)) break;
                 if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
                 ptx::tc_fence_after();
-                const uint32_t ahi = tmem_a + (uint32_t)(st * A_COLS);
-                const uint32_t alo = ahi + (uint32_t)K;
-                const uint32_t d = tmem_d + (uint32_t)(st * N);
-                if (args.nprod > 1) {
-#pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        ptx::mma_tf32_ts(d, alo + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, ks > 0);
-#pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        ptx::mma_tf32_ts(d, ahi + 8 * ks, blo0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, 1u);
-                }
-#pragma unroll
-                for (int ks = 0; ks < KS; ++ks)
-                    ptx::mma_tf32_ts(d, ahi + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc,
-                                     (args.nprod > 1 || ks > 0) ? 1u : 0u);
+                issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(st * A_COLS), PC, b0,
+                                       args.bpart_bytes, N, idesc, pr);
                 ptx::mma_commit(&aempty[st]);
                 ptx::mma_commit(&accf[st]);
                 committed = i;
@@ -249,32 +245,28 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 const bool fix = (args.bc == kBcPeriodic) &&
                                  (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
                 const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
-                const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
-                const uint32_t alo = ahi + (uint32_t)K;
+                const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
 #pragma unroll
                 for (int g0 = 0; g0 < NG; g0 += kSubs) {
                     const int g = g0 + sub;
                     if (g >= NG) break;
-                    const int c8 = 8 * g;
-                    float4 v0 = *reinterpret_cast<const float4*>(row + c8);
-                    float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
-                    if (fix) {
-                        const int64_t wy = wrap_index(gy, args.ny);
-                        const int gx0 = X0 - kPad + c8;
-                        if (gy < 0 || gy >= args.ny || gx0 < 0 || gx0 >= args.nx)
-                            v0 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0, args.nx));
-                        if (gy < 0 || gy >= args.ny || gx0 + 4 < 0 || gx0 + 4 >= args.nx)
-                            v1 = *reinterpret_cast<const float4*>(args.in + wy * args.nx + wrap_index(gx0 + 4, args.nx));
-                    }
-                    const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    uint32_t h[8], l[8];
+                    const int c0 = GW * g;
+                    float x[GW];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        h[e] = tf32_hi_bits(x[e]);
-                        l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+                    for (int c4 = 0; c4 < GW; c4 += 4) {
+                        float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
+                        if (fix) {
+                            const int gx = X0 - kPad + c0 + c4;
+                            if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
+                                v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
+                                                                     wrap_index(gx, args.nx));
+                        }
+                        x[c4] = v.x;
+                        x[c4 + 1] = v.y;
+                        x[c4 + 2] = v.z;
+                        x[c4 + 3] = v.w;
                     }
-                    ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
-                    if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
+                    split_store<BF>(x, abase, PC, c0, args.nparts);
                 }
                 ptx::tmem_wait_st();
                 ptx::tc_fence_before();
@@ -374,9 +366,9 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     }
 }
 
-template <int R>
+template <int R, bool BF>
 constexpr auto kernel_for() {
-    return mx2d_kernel<R, tile_nb(2 * R + 1)>;
+    return mx2d_kernel<R, tile_nb<BF>(2 * R + 1), BF>;
 }
 
 // ------------------------------------------------------------------ host side
@@ -411,12 +403,12 @@ bool encode_out_map_2d(CUtensorMap* map, float* base, int ny, int nx, int nb, in
 
 using MxKernel = void (*)(CUtensorMap, CUtensorMap, MxArgs2D);
 
-MxKernel kernel_for_radius(int r) {
+MxKernel kernel_for_radius(int r, bool bf) {
     switch (r) {
-        case 1: return kernel_for<1>();
-        case 2: return kernel_for<2>();
-        case 3: return kernel_for<3>();
-        case 4: return kernel_for<4>();
+        case 1: return bf ? kernel_for<1, true>() : kernel_for<1, false>();
+        case 2: return bf ? kernel_for<2, true>() : kernel_for<2, false>();
+        case 3: return bf ? kernel_for<3, true>() : kernel_for<3, false>();
+        case 4: return bf ? kernel_for<4, true>() : kernel_for<4, false>();
     }
     return nullptr;
 }
@@ -426,7 +418,10 @@ struct MxState {
     unsigned int* err_dev = nullptr;
     int num_sms = 0;
     int nb = 32;          // output columns per tile
+    int in_w = 40;        // input columns per tile (the K window)
+    bool bf = false;      // BF16 operands (else TF32)
     uint32_t bop_bytes = 0;
+    uint32_t bpart_bytes = 0;
 };
 
 }  // namespace
@@ -437,8 +432,8 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         return false;
     }
     if (q.ndim == 3) return mx3d_supported(q, why);
-    if (q.prec != STENCIL_PREC_TF32 && q.prec != STENCIL_PREC_TF32X3) {
-        if (why) *why = "only TF32 and TF32X3 outer products are built for 2D";
+    if (q.prec < STENCIL_PREC_TF32 || q.prec > STENCIL_PREC_BF16X3) {
+        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2 or BF16X3";
         return false;
     }
     if (q.n[1] % 4 != 0) {
@@ -463,29 +458,17 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     if (q.ndim == 3) return mx3d_plan_build(q, p, why);
     const int W = 2 * q.r + 1;
     const int L = W;            // every row a of C^g is one line along the contiguous axis
-    const int NB = tile_nb(L);
-    const int KW = NB + 2 * kPad;
-    const int N = L * NB;
+    const bool bf = is_bf16(q.prec);
+    const int NB = bf ? tile_nb<true>(L) : tile_nb<false>(L);
+    const int KW = bf ? OpFmt<true>::window(NB) : OpFmt<false>::window(NB);
     p->nb = NB;
-    // B operand, N x K, K-major core matrices: [part][kchunk][n = a*NB + q][4];
-    // entry (n, k) = H_a[k][q] = C^g[a][k - q - (kPad - r)] (banded, Eq. (co)).
-    const size_t part_floats = (size_t)(KW / 4) * N * 4;
-    std::vector<float> ops(2 * part_floats, 0.0f);
-    for (int a = 0; a < L; ++a) {
-        std::vector<double> band((size_t)KW * NB);
-        band_operand(q.r, q.cg + a * W, NB, kPad, band.data());
-        for (int k = 0; k < KW; ++k)
-            for (int qq = 0; qq < NB; ++qq) {
-                const float h = (float)band[(size_t)k * NB + qq];
-                const float hi = tf32_round(h);
-                const size_t off = (size_t)(k / 4) * N * 4 + (size_t)(a * NB + qq) * 4 + (k % 4);
-                ops[off] = hi;
-                ops[part_floats + off] = tf32_round(h - hi);
-            }
-    }
+    std::vector<const double*> lines;
+    for (int a = 0; a < L; ++a) lines.push_back(q.cg + a * W);
+    uint32_t bpart = 0;
+    std::vector<unsigned char> ops = pack_bands(q.r, lines, NB, KW, bf, &bpart);
     p->n_lines = L;
     p->n_scalar = 0;
-    p->operand_bytes = ops.size() * sizeof(float);
+    p->operand_bytes = ops.size();
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {
         if (why) *why = std::string("operand upload: ") + cudaGetErrorString(e);
@@ -500,7 +483,10 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     }
     MxState* st = new MxState();
     st->bop_bytes = (uint32_t)p->operand_bytes;
+    st->bpart_bytes = bpart;
     st->nb = NB;
+    st->in_w = KW;
+    st->bf = bf;
     e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
     if (e != cudaSuccess) {
@@ -520,8 +506,8 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
         if (why) *why = std::string("device query: ") + cudaGetErrorString(e);
         return STENCIL_ECUDA;
     }
-    const size_t smem = smem_bytes_2d(st->nb + 2 * kPad, st->bop_bytes);
-    e = cudaFuncSetAttribute(kernel_for_radius(q.r), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = smem_bytes_2d(st->nb, st->in_w, st->bop_bytes);
+    e = cudaFuncSetAttribute(kernel_for_radius(q.r, bf), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         mx_plan_free(p);
         if (why) *why = std::string("shared memory: ") + cudaGetErrorString(e);
@@ -561,13 +547,15 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     memset(&a, 0, sizeof(a));
     a.out = (float*)dst;
     a.in = (const float*)src;
-    a.bops = (const float*)p.d_operands;
+    a.bops = p.d_operands;
     a.err = st->err_dev;
     a.ny = ny;
     a.nx = nx;
     a.bc = p.bc;
-    a.nprod = (p.prec == STENCIL_PREC_TF32X3) ? 3 : 1;
-    const int in_w = st->nb + 2 * kPad;
+    a.nparts = operand_parts(p.prec);
+    a.prods = products_for(p.prec);
+    a.bpart_bytes = st->bpart_bytes;
+    const int in_w = st->in_w;
     a.tiles_x = (nx + st->nb - 1) / st->nb;
     const int tile_rows = kQuarters * (kSlabRows - 2 * p.r);
     a.tiles_total = a.tiles_x * ((ny + tile_rows - 1) / tile_rows);
@@ -577,7 +565,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, in_w)) return cudaErrorInvalidValue;
     if (!encode_out_map_2d(&map_out, (float*)dst, ny, nx, st->nb, tile_rows)) return cudaErrorInvalidValue;
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    kernel_for_radius(p.r)<<<grid, kThreads, smem_bytes_2d(in_w, a.bop_bytes), s>>>(map, map_out, a);
+    kernel_for_radius(p.r, st->bf)<<<grid, kThreads, smem_bytes_2d(st->nb, in_w, a.bop_bytes), s>>>(map, map_out, a);
     return cudaGetLastError();
 }
 

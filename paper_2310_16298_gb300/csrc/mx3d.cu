@@ -59,36 +59,48 @@ struct Lines3 {
     __host__ __device__ static constexpr int b(int l) { return STAR ? (l < R || l >= R + W ? R : l - R) : l % W; }
 };
 
-__host__ __device__ constexpr int tile_nb3(int L) { return (2 * L * 32 + 4 * (32 + 2 * kPad) <= kTmemCols) ? 32 : 16; }
+template <bool BF>
+__host__ __device__ constexpr int a_stage_cols3(int nb) {
+    return OpFmt<BF>::kMaxParts * OpFmt<BF>::part_cols(OpFmt<BF>::window(nb));
+}
+template <bool BF>
+__host__ __device__ constexpr int tile_nb3(int L) {
+    return (L * 32 <= 256 && 2 * L * 32 + 2 * a_stage_cols3<BF>(32) <= kTmemCols) ? 32 : 16;
+}
 __host__ __device__ constexpr int raw_stage_bytes3(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
 __host__ __device__ constexpr int out_stage_bytes3(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
 
-size_t smem_bytes_3d(int in_w, uint32_t bop_bytes) {
-    return 1024 + (size_t)kRawStages * raw_stage_bytes3(in_w) + 2 * (size_t)out_stage_bytes3(in_w - 8) + bop_bytes +
+size_t smem_bytes_3d(int nb, int in_w, uint32_t bop_bytes) {
+    return 1024 + (size_t)kRawStages * raw_stage_bytes3(in_w) + 2 * (size_t)out_stage_bytes3(nb) + bop_bytes +
            8 * (2 * kRawStages + 16);
 }
 
 struct MxArgs3D {
-    const float* bops;    // banded operands [part][kchunk][line*NB + q][4]
+    const void* bops;     // banded operands [part][kchunk][line*NB + q][16 bytes]
     unsigned int* err;    // device error word (host-mapped)
     int nz, ny, nx;
-    int nprod;            // 1 (TF32) or 3 (TF32x3)
+    int nparts;           // operand parts of the input split (1..3)
     int tiles_x, tiles_y, chunks, units;
     uint32_t bop_bytes;
+    uint32_t bpart_bytes;
+    Products prods;
 };
 
-template <int R, bool STAR, int NB>
+template <int R, bool STAR, int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
             const MxArgs3D args) {
     using LN = Lines3<R, STAR>;
+    using F = OpFmt<BF>;
     constexpr int L = LN::L;
     constexpr int N = L * NB;
-    constexpr int K = NB + 2 * kPad;
-    constexpr int KS = K / 8;
-    constexpr int NG = K / 8;
+    constexpr int K = F::window(NB);
+    constexpr int KS = K / F::kKStep;
+    constexpr int GW = F::kGroup;
+    constexpr int NG = K / GW;
     constexpr int ROWS_OUT = kSlabRows - 2 * R;
-    constexpr int A_COLS = 2 * K;
+    constexpr int PC = F::part_cols(K);
+    constexpr int A_COLS = F::kMaxParts * PC;
     constexpr int CW = NB / kSubs;
     constexpr int RSB = raw_stage_bytes3(K);
     constexpr int OSB = out_stage_bytes3(NB);
@@ -180,10 +192,9 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         }
     } else if (warp == 1) {
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
-            constexpr uint32_t idesc = ptx::instr_desc(2, 2, 128, (uint32_t)N);
-            const uint32_t part_bytes = args.bop_bytes / 2;
-            const uint64_t bhi0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
-            const uint64_t blo0 = bhi0 + (uint64_t)(part_bytes >> 4);
+            constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
+            const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
+            const Products pr = args.prods;
             int i = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
@@ -195,21 +206,8 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t ahi = tmem_a + (uint32_t)(st * A_COLS);
-                    const uint32_t alo = ahi + (uint32_t)K;
-                    const uint32_t d = tmem_d + (uint32_t)(st * N);
-                    if (args.nprod > 1) {
-#pragma unroll
-                        for (int ks = 0; ks < KS; ++ks)
-                            ptx::mma_tf32_ts(d, alo + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, ks > 0);
-#pragma unroll
-                        for (int ks = 0; ks < KS; ++ks)
-                            ptx::mma_tf32_ts(d, ahi + 8 * ks, blo0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc, 1u);
-                    }
-#pragma unroll
-                    for (int ks = 0; ks < KS; ++ks)
-                        ptx::mma_tf32_ts(d, ahi + 8 * ks, bhi0 + (uint64_t)((2 * ks * N * 16) >> 4), idesc,
-                                         (args.nprod > 1 || ks > 0) ? 1u : 0u);
+                    issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(st * A_COLS), PC, b0,
+                                           args.bpart_bytes, N, idesc, pr);
                     ptx::mma_commit(&aempty[st]);
                     ptx::mma_commit(&accf[st]);
                     committed = i;
@@ -236,24 +234,22 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     }
                     ptx::tc_fence_after();
                     const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
-                    const uint32_t ahi = tmem_a + lane_off + (uint32_t)(st * A_COLS);
-                    const uint32_t alo = ahi + (uint32_t)K;
+                    const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
 #pragma unroll
                     for (int g0 = 0; g0 < NG; g0 += kSubs) {
                         const int g = g0 + sub;
                         if (g >= NG) break;
-                        const int c8 = 8 * g;
-                        const float4 v0 = *reinterpret_cast<const float4*>(row + c8);
-                        const float4 v1 = *reinterpret_cast<const float4*>(row + c8 + 4);
-                        const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                        uint32_t h[8], l[8];
+                        const int c0 = GW * g;
+                        float x[GW];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            h[e] = tf32_hi_bits(x[e]);
-                            l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+                        for (int c4 = 0; c4 < GW; c4 += 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
+                            x[c4] = v.x;
+                            x[c4 + 1] = v.y;
+                            x[c4 + 2] = v.z;
+                            x[c4 + 3] = v.w;
                         }
-                        ptx::tmem_st_32x32b_x8(ahi + (uint32_t)c8, h);
-                        if (args.nprod > 1) ptx::tmem_st_32x32b_x8(alo + (uint32_t)c8, l);
+                        split_store<BF>(x, abase, PC, c0, args.nparts);
                     }
                     ptx::tmem_wait_st();
                     ptx::tc_fence_before();
@@ -385,20 +381,20 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
 
 using Mx3Kernel = void (*)(CUtensorMap, CUtensorMap, MxArgs3D);
 
-template <int R, bool STAR>
+template <int R, bool STAR, bool BF>
 Mx3Kernel kernel3() {
-    return mx3d_kernel<R, STAR, tile_nb3(Lines3<R, STAR>::L)>;
+    return mx3d_kernel<R, STAR, tile_nb3<BF>(Lines3<R, STAR>::L), BF>;
 }
 
-Mx3Kernel kernel3_for(int r, bool star) {
+Mx3Kernel kernel3_for(int r, bool star, bool bf) {
     if (star) {
         switch (r) {
-            case 1: return kernel3<1, true>();
-            case 2: return kernel3<2, true>();
-            case 3: return kernel3<3, true>();
+            case 1: return bf ? kernel3<1, true, true>() : kernel3<1, true, false>();
+            case 2: return bf ? kernel3<2, true, true>() : kernel3<2, true, false>();
+            case 3: return bf ? kernel3<3, true, true>() : kernel3<3, true, false>();
         }
     } else if (r == 1) {
-        return kernel3<1, false>();
+        return bf ? kernel3<1, false, true>() : kernel3<1, false, false>();
     }
     return nullptr;
 }
@@ -442,22 +438,25 @@ struct Mx3State {
     unsigned int* err_dev = nullptr;
     int num_sms = 0;
     int nb = 16;
+    int in_w = 24;
     bool star = false;
+    bool bf = false;
     uint32_t bop_bytes = 0;
+    uint32_t bpart_bytes = 0;
 };
 
 }  // namespace
 
 bool mx3d_supported(const MxRequest& q, std::string* why) {
-    if (q.prec != STENCIL_PREC_TF32 && q.prec != STENCIL_PREC_TF32X3) {
-        if (why) *why = "only TF32 and TF32X3 outer products are built for 3D";
+    if (q.prec < STENCIL_PREC_TF32 || q.prec > STENCIL_PREC_BF16X3) {
+        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2 or BF16X3";
         return false;
     }
     if (q.bc != kBcDirichlet) {
         if (why) *why = "the 3D matrixized kernel handles the zero Dirichlet boundary only";
         return false;
     }
-    if (!kernel3_for(q.r, q.star)) {
+    if (!kernel3_for(q.r, q.star, false)) {
         if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27-point box";
         return false;
     }
@@ -476,28 +475,18 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     if (!mx3d_supported(q, why)) return STENCIL_EUNSUPPORTED;
     const int r = q.r, W = 2 * r + 1;
     const int L = lines3(r, q.star);
-    const int NB = tile_nb3(L);
-    const int KW = NB + 2 * kPad;
-    const int N = L * NB;
+    const bool bf = is_bf16(q.prec);
+    const int NB = bf ? tile_nb3<true>(L) : tile_nb3<false>(L);
+    const int KW = bf ? OpFmt<true>::window(NB) : OpFmt<false>::window(NB);
     p->nb = NB;
-    const size_t part_floats = (size_t)(KW / 4) * N * 4;
-    std::vector<float> ops(2 * part_floats, 0.0f);
-    for (int l = 0; l < L; ++l) {
-        const int a = line3_a(r, q.star, l), b = line3_b(r, q.star, l);
-        std::vector<double> band((size_t)KW * NB);
-        band_operand(r, q.cg + ((size_t)a * W + b) * W, NB, kPad, band.data());
-        for (int k = 0; k < KW; ++k)
-            for (int qq = 0; qq < NB; ++qq) {
-                const float h = (float)band[(size_t)k * NB + qq];
-                const float hi = tf32_round(h);
-                const size_t off = (size_t)(k / 4) * N * 4 + (size_t)(l * NB + qq) * 4 + (k % 4);
-                ops[off] = hi;
-                ops[part_floats + off] = tf32_round(h - hi);
-            }
-    }
+    std::vector<const double*> lines;
+    for (int l = 0; l < L; ++l)
+        lines.push_back(q.cg + ((size_t)line3_a(r, q.star, l) * W + line3_b(r, q.star, l)) * W);
+    uint32_t bpart = 0;
+    std::vector<unsigned char> ops = pack_bands(r, lines, NB, KW, bf, &bpart);
     p->n_lines = L;
     p->n_scalar = 0;
-    p->operand_bytes = ops.size() * sizeof(float);
+    p->operand_bytes = ops.size();
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {
         if (why) *why = std::string("operand upload: ") + cudaGetErrorString(e);
@@ -506,16 +495,19 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     e = cudaMemcpy(p->d_operands, ops.data(), p->operand_bytes, cudaMemcpyHostToDevice);
     Mx3State* st = new Mx3State();
     st->nb = NB;
+    st->in_w = KW;
     st->star = q.star;
+    st->bf = bf;
     st->bop_bytes = (uint32_t)p->operand_bytes;
+    st->bpart_bytes = bpart;
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel3_for(r, q.star), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes_3d(KW, st->bop_bytes));
+        e = cudaFuncSetAttribute(kernel3_for(r, q.star, bf), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes_3d(NB, KW, st->bop_bytes));
     p->tmap_storage = st;
     if (e != cudaSuccess) {
         if (why) *why = std::string("3D plan set-up: ") + cudaGetErrorString(e);
@@ -547,16 +539,18 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     if (((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return cudaErrorMisalignedAddress;
     const Mx3State* st = (const Mx3State*)p.tmap_storage;
     const int nz = (int)p.n[0], ny = (int)p.n[1], nx = (int)p.n[2];
-    const int in_w = st->nb + 2 * kPad;
+    const int in_w = st->in_w;
     const int rows_tile = kQuarters * (kSlabRows - 2 * p.r);
     MxArgs3D a;
     memset(&a, 0, sizeof(a));
-    a.bops = (const float*)p.d_operands;
+    a.bops = p.d_operands;
     a.err = st->err_dev;
     a.nz = nz;
     a.ny = ny;
     a.nx = nx;
-    a.nprod = (p.prec == STENCIL_PREC_TF32X3) ? 3 : 1;
+    a.nparts = operand_parts(p.prec);
+    a.prods = products_for(p.prec);
+    a.bpart_bytes = st->bpart_bytes;
     a.tiles_x = (nx + st->nb - 1) / st->nb;
     a.tiles_y = (ny + rows_tile - 1) / rows_tile;
     a.chunks = (nz + kChunk - 1) / kChunk;
@@ -566,7 +560,8 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, in_w)) return cudaErrorInvalidValue;
     if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb, rows_tile)) return cudaErrorInvalidValue;
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
-    kernel3_for(p.r, st->star)<<<grid, kThreads, smem_bytes_3d(in_w, a.bop_bytes), s>>>(map, map_out, a);
+    kernel3_for(p.r, st->star, st->bf)<<<grid, kThreads, smem_bytes_3d(st->nb, in_w, a.bop_bytes), s>>>(map, map_out,
+                                                                                                     a);
     return cudaGetLastError();
 }
 

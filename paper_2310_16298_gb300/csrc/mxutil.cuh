@@ -6,7 +6,11 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
+#include "plan.h"
+
+#include "../../include/stencil.h"
 #include "ptx.cuh"
 
 namespace stx {
@@ -33,6 +37,118 @@ __device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
     return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
+// BF16 bits (upper half of the FP32 pattern) of x rounded to nearest, ties to
+// even; finite inputs.
+__device__ __forceinline__ uint32_t bf16_rn_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+
+// Operand formats of the matrixized kernels.  Both use, per MMA K-step, 8
+// tensor-memory columns of A and two 16-byte chunks of B:
+//   TF32 (kind::tf32): one element per column, K = 8 per MMA, parts hi/lo;
+//   BF16 (kind::f16):  two elements per column, K = 16 per MMA, parts 0/1/2.
+template <bool BF>
+struct OpFmt {
+    static constexpr int kKStep = BF ? 16 : 8;          // K per MMA
+    static constexpr int kGroup = BF ? 16 : 8;          // input columns per tcgen05.st x8
+    static constexpr uint32_t kFmt = BF ? 1u : 2u;      // instruction-descriptor A/B format
+    static constexpr int kMaxParts = BF ? 3 : 2;
+    __host__ __device__ static constexpr int window(int nb) {  // K window for nb outputs
+        return ((nb + 8) + kKStep - 1) / kKStep * kKStep;
+    }
+    __host__ __device__ static constexpr int part_cols(int k) { return BF ? k / 2 : k; }
+};
+
+// The products of one precision mode: (A part, B part) pairs, smallest first.
+struct Products {
+    int n;
+    int a[6];
+    int b[6];
+};
+
+inline Products products_for(int prec) {
+    switch (prec) {
+        case STENCIL_PREC_TF32: return {1, {0}, {0}};
+        case STENCIL_PREC_TF32X3: return {3, {1, 0, 0}, {0, 1, 0}};
+        case STENCIL_PREC_BF16: return {1, {0}, {0}};
+        case STENCIL_PREC_BF16X2: return {3, {1, 0, 0}, {0, 1, 0}};
+        case STENCIL_PREC_BF16X3: return {6, {0, 1, 2, 1, 0, 0}, {2, 1, 0, 0, 1, 0}};
+    }
+    return {0, {0}, {0}};
+}
+
+inline int operand_parts(int prec) {
+    switch (prec) {
+        case STENCIL_PREC_TF32X3: return 2;
+        case STENCIL_PREC_BF16X2: return 2;
+        case STENCIL_PREC_BF16X3: return 3;
+    }
+    return 1;
+}
+
+inline bool is_bf16(int prec) {
+    return prec == STENCIL_PREC_BF16 || prec == STENCIL_PREC_BF16X2 || prec == STENCIL_PREC_BF16X3;
+}
+
+// Issue every product of one tile (A in tensor memory, B in shared memory)
+// into accumulator d: product p uses A part pa[p] and B part pb[p]; all K
+// steps of a product are issued before the next product.
+template <bool BF, int KS>
+__device__ __forceinline__ void issue_products(uint32_t d, uint32_t a_base, int part_cols, uint64_t b_desc0,
+                                               uint32_t bpart_bytes, int n, uint32_t idesc, const Products& pr) {
+    for (int p = 0; p < pr.n; ++p) {
+        const uint32_t a = a_base + (uint32_t)(pr.a[p] * part_cols);
+        const uint64_t b = b_desc0 + (uint64_t)((pr.b[p] * bpart_bytes) >> 4);
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const uint64_t bd = b + (uint64_t)((2 * ks * n * 16) >> 4);
+            const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
+            if constexpr (BF) {
+                ptx::mma_f16_ts(d, a + 8 * ks, bd, idesc, acc);
+            } else {
+                ptx::mma_tf32_ts(d, a + 8 * ks, bd, idesc, acc);
+            }
+        }
+    }
+}
+
+// Split kGroup input values into the operand parts and write them to the
+// warp's tensor-memory lanes at column c (part p at a_base + p*part_cols).
+template <bool BF>
+__device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int part_cols, int c, int nparts) {
+    if constexpr (!BF) {
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            h[e] = tf32_hi_bits(x[e]);
+            l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+        }
+        ptx::tmem_st_32x32b_x8(a_base + (uint32_t)c, h);
+        if (nparts > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c), l);
+    } else {
+        uint32_t w[3][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            float r0a = x[2 * e], r0b = x[2 * e + 1];
+            uint32_t pa[3], pb[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint32_t ba = bf16_rn_bits(r0a), bb = bf16_rn_bits(r0b);
+                pa[k] = ba;
+                pb[k] = bb;
+                r0a -= __uint_as_float(ba << 16);
+                r0b -= __uint_as_float(bb << 16);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) w[k][e] = pa[k] | (pb[k] << 16);
+        }
+        ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(c / 2), w[0]);
+        if (nparts > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c / 2), w[1]);
+        if (nparts > 2) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(2 * part_cols + c / 2), w[2]);
+    }
+}
 
 inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -49,6 +165,17 @@ inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 
+// Round to BF16 on the host (nearest, ties to even); finite inputs.
+inline float bf16_round(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
 // Round to TF32 on the host (nearest, ties to even); finite inputs.
 inline float tf32_round(float x) {
     uint32_t u;
@@ -60,6 +187,45 @@ inline float tf32_round(float x) {
     return y;
 }
 
+
+// Pack the banded operands of the given lines (line l: 2r+1 gather weights)
+// as the MMA B operand, N = lines x nb rows, K-major 16-byte chunks:
+// [part][k chunk][n = l*nb + q][16 bytes].  Row (n, k) holds the band entry
+// H_l[k][q] = w_l[k - q - (4 - r)] (zero outside the band and for k >= nb + 8),
+// split into TF32 hi/lo parts or three BF16 parts.  Returns the bytes of one
+// part in *part_bytes.
+inline std::vector<unsigned char> pack_bands(int r, const std::vector<const double*>& lines, int nb, int kwin, bool bf,
+                                             uint32_t* part_bytes) {
+    const int L = (int)lines.size(), N = L * nb;
+    const int epc = bf ? 8 : 4;  // elements per 16-byte chunk
+    const int es = bf ? 2 : 4;
+    const int parts = bf ? 3 : 2;
+    const size_t pb = (size_t)(kwin / epc) * N * 16;
+    std::vector<unsigned char> out(parts * pb, 0);
+    std::vector<double> band((size_t)(nb + 8) * nb);
+    for (int l = 0; l < L; ++l) {
+        band_operand(r, lines[l], nb, 4, band.data());
+        for (int k = 0; k < nb + 8; ++k)
+            for (int q = 0; q < nb; ++q) {
+                float rem = (float)band[(size_t)k * nb + q];
+                const size_t off = ((size_t)(k / epc) * N + (size_t)(l * nb + q)) * 16 + (size_t)(k % epc) * es;
+                for (int p = 0; p < parts; ++p) {
+                    const float v = bf ? bf16_round(rem) : tf32_round(rem);
+                    rem -= v;
+                    if (bf) {
+                        uint32_t u;
+                        memcpy(&u, &v, 4);
+                        const uint16_t h = (uint16_t)(u >> 16);
+                        memcpy(&out[p * pb + off], &h, 2);
+                    } else {
+                        memcpy(&out[p * pb + off], &v, 4);
+                    }
+                }
+            }
+    }
+    *part_bytes = (uint32_t)pb;
+    return out;
+}
 
 }  // namespace mxu
 }  // namespace stx

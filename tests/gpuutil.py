@@ -10,8 +10,11 @@ import paper_2310_16298_gb300 as sx
 GUARD = 4096  # elements of canary before and after each output grid
 CANARY = 1234.5
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-5, "bf16x2": 1e-5, "tf32": 1e-3,
-       "bf16": 1e-3}
+# Tolerances on rel-L2 and rel-max against the FP64 oracle.  Plain TF32 and
+# the BF16 family are set from their operand mantissas (TF32 11 bits, BF16 8,
+# BF16x2 16, BF16x3 24).
+TOL = {"f64": 1e-12, "f32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-5, "bf16x2": 1e-4, "tf32": 1e-3,
+       "bf16": 1e-2}
 
 
 def torch_dtype(dtype):

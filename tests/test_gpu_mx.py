@@ -16,7 +16,7 @@ def problem(ndim, shape, r, kind, seed, lo=-1.0, hi=1.0):
     return a, cg
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16x2", "bf16"])
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 @pytest.mark.parametrize("kind", ["box", "star"])
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
@@ -84,7 +84,7 @@ def test_mx_rejects_unaligned_rows():
     assert ei.value.status == sx.EUNSUPPORTED
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16"])
 @pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("star", 3)])
 @pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
 def test_mx_3d(prec, kind, r, shape):
@@ -116,3 +116,15 @@ def test_mx_3d_symmetric_closed_form():
     check(got, oracle.gather(f, 1, cg, "dirichlet", T), 1e-5, "3d sine mode")
     l2, _ = oracle.error_norms(got, lam ** T * f)
     assert l2 < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+def test_mx_bf16_exact_operands(prec):
+    """Inputs and weights exactly representable in BF16: the lower parts vanish
+    and the split products reproduce the FP32 result to 1e-6."""
+    rng = np.random.default_rng(2)
+    shape = (140, 64)
+    a = rng.integers(-16, 17, size=shape) / 16.0
+    cg = rng.integers(-8, 9, size=(5, 5)) / 64.0
+    got, _ = run(a, 2, "box", cg, "f32", "periodic", 2, impl="matrixized", prec=prec)
+    check(got, oracle.gather(a, 2, cg, "periodic", 2), 1e-6, f"{prec} exact operands")
