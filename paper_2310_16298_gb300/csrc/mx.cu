@@ -78,7 +78,7 @@ struct MxArgs2D {
     int tiles_x, tiles_total;
     uint32_t bop_bytes;        // every part
     uint32_t bpart_bytes;      // one part
-    Products prods;            // (A part, B part) products, smallest first
+    int nprod;                 // products per K step (1, 3 or 6)
 };
 
 __host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
@@ -207,7 +207,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
             constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
-            const Products pr = args.prods;
+            const int pr = args.nprod;
             int i = 0;
             for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
                 const int st = i & 1;
@@ -553,7 +553,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.nx = nx;
     a.bc = p.bc;
     a.nparts = operand_parts(p.prec);
-    a.prods = products_for(p.prec);
+    a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;
     const int in_w = st->in_w;
     a.tiles_x = (nx + st->nb - 1) / st->nb;

@@ -83,7 +83,7 @@ struct MxArgs3D {
     int tiles_x, tiles_y, chunks, units;
     uint32_t bop_bytes;
     uint32_t bpart_bytes;
-    Products prods;
+    int nprod;
 };
 
 template <int R, bool STAR, int NB, bool BF>
@@ -194,7 +194,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
             constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
-            const Products pr = args.prods;
+            const int pr = args.nprod;
             int i = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
@@ -549,7 +549,7 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     a.ny = ny;
     a.nx = nx;
     a.nparts = operand_parts(p.prec);
-    a.prods = products_for(p.prec);
+    a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;
     a.tiles_x = (nx + st->nb - 1) / st->nb;
     a.tiles_y = (ny + rows_tile - 1) / rows_tile;

@@ -61,22 +61,14 @@ struct OpFmt {
     __host__ __device__ static constexpr int part_cols(int k) { return BF ? k / 2 : k; }
 };
 
-// The products of one precision mode: (A part, B part) pairs, smallest first.
-struct Products {
-    int n;
-    int a[6];
-    int b[6];
-};
-
-inline Products products_for(int prec) {
+// Products per K step of a precision mode (see issue_products).
+inline int products_for(int prec) {
     switch (prec) {
-        case STENCIL_PREC_TF32: return {1, {0}, {0}};
-        case STENCIL_PREC_TF32X3: return {3, {1, 0, 0}, {0, 1, 0}};
-        case STENCIL_PREC_BF16: return {1, {0}, {0}};
-        case STENCIL_PREC_BF16X2: return {3, {1, 0, 0}, {0, 1, 0}};
-        case STENCIL_PREC_BF16X3: return {6, {0, 1, 2, 1, 0, 0}, {2, 1, 0, 0, 1, 0}};
+        case STENCIL_PREC_TF32X3: return 3;
+        case STENCIL_PREC_BF16X2: return 3;
+        case STENCIL_PREC_BF16X3: return 6;
     }
-    return {0, {0}, {0}};
+    return 1;
 }
 
 inline int operand_parts(int prec) {
@@ -92,26 +84,41 @@ inline bool is_bf16(int prec) {
     return prec == STENCIL_PREC_BF16 || prec == STENCIL_PREC_BF16X2 || prec == STENCIL_PREC_BF16X3;
 }
 
-// Issue every product of one tile (A in tensor memory, B in shared memory)
-// into accumulator d: product p uses A part pa[p] and B part pb[p]; all K
-// steps of a product are issued before the next product.
+// Issue every K step of one product (A part pa, B part pb) into accumulator
+// d; `first` clears the accumulator with the first step.
 template <bool BF, int KS>
-__device__ __forceinline__ void issue_products(uint32_t d, uint32_t a_base, int part_cols, uint64_t b_desc0,
-                                               uint32_t bpart_bytes, int n, uint32_t idesc, const Products& pr) {
-    for (int p = 0; p < pr.n; ++p) {
-        const uint32_t a = a_base + (uint32_t)(pr.a[p] * part_cols);
-        const uint64_t b = b_desc0 + (uint64_t)((pr.b[p] * bpart_bytes) >> 4);
+__device__ __forceinline__ void issue_product(uint32_t d, uint32_t a_base, int part_cols, uint64_t b_desc0,
+                                              uint32_t bpart_bytes, int n, uint32_t idesc, int pa, int pb, bool first) {
+    const uint32_t a = a_base + (uint32_t)(pa * part_cols);
+    const uint64_t b = b_desc0 + (uint64_t)((pb * bpart_bytes) >> 4);
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            const uint64_t bd = b + (uint64_t)((2 * ks * n * 16) >> 4);
-            const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
-            if constexpr (BF) {
-                ptx::mma_f16_ts(d, a + 8 * ks, bd, idesc, acc);
-            } else {
-                ptx::mma_tf32_ts(d, a + 8 * ks, bd, idesc, acc);
-            }
+    for (int ks = 0; ks < KS; ++ks) {
+        const uint64_t bd = b + (uint64_t)((2 * ks * n * 16) >> 4);
+        const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+        if constexpr (BF) {
+            ptx::mma_f16_ts(d, a + 8 * ks, bd, idesc, acc);
+        } else {
+            ptx::mma_tf32_ts(d, a + 8 * ks, bd, idesc, acc);
         }
     }
+}
+
+// Issue every product of one tile (A in tensor memory, B in shared memory)
+// into accumulator d, smallest products first: nprod = 1 (x0*h0), 3 (x1*h0,
+// x0*h1, x0*h0) or 6 (x0*h2, x1*h1, x2*h0, x1*h0, x0*h1, x0*h0).
+template <bool BF, int KS>
+__device__ __forceinline__ void issue_products(uint32_t d, uint32_t a_base, int pc, uint64_t b0, uint32_t bpb,
+                                               int n, uint32_t idesc, int nprod) {
+    if (nprod == 6) {
+        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 2, true);
+        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 1, 1, false);
+        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 2, 0, false);
+    }
+    if (nprod >= 3) {
+        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 1, 0, nprod == 3);
+        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 1, false);
+    }
+    issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 0, nprod == 1);
 }
 
 // Split kGroup input values into the operand parts and write them to the
