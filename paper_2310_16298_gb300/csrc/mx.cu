@@ -55,8 +55,9 @@ constexpr int kRoleWarps = 8;           // warps per role: two per lane quarter
 constexpr int kSubs = 2;                // warps of one role per lane quarter
 constexpr int kThreads = 64 + 32 * kMathWarps;  // producer warp, MMA warp, math warps
 constexpr int kMathThreads = 32 * kMathWarps;
-constexpr int kRawStages = 6;           // TMA ring depth
+constexpr int kMaxRawStages = 6;        // TMA ring depth (fewer where shared memory runs out)
 constexpr int kTmemCols = 512;
+constexpr int kSmemBudget = 227 * 1024;
 
 // Output columns per tile (the MMA block width) for a stencil with L lines:
 // 32 while both accumulator sets (2 x L x 32 columns) and both A stages fit
@@ -81,15 +82,42 @@ struct MxArgs2D {
     int nprod;                 // products per K step (1, 3 or 6)
 };
 
-__host__ __device__ constexpr int raw_stage_bytes(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
+// Shared-memory row pitch of the raw input tile: the K window widened to an
+// odd number of 16-byte chunks, so that the 16-byte loads of eight
+// consecutive rows (one shared-memory wavefront) fall in eight distinct bank
+// groups.  The extra columns are loaded by TMA and never read.
+__host__ __device__ constexpr int raw_pitch(int k) { return ((k / 4) & 1) ? k : k + 4; }
+__host__ __device__ constexpr int raw_stage_bytes(int pitch) { return kQuarters * kSlabRows * pitch * 4; }
 
-// Output staging for the TMA store: 2 stages of 4 x (32 - 2r) rows x NB
-// floats, each stage padded to 1 KB (the swizzle span).
-__host__ __device__ constexpr int out_stage_bytes(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
+// Output staging: every epilogue warp owns two buffers of (32 - 2r) rows x
+// NB/2 floats (its share of the tile), each padded to 1 KB, and writes them
+// with its own TMA store.
+__host__ __device__ constexpr int out_warp_bytes(int nb) { return ((32 * (nb / kSubs) * 4) + 1023) / 1024 * 1024; }
+__host__ __device__ constexpr int out_bytes_2d(int nb) { return kRoleWarps * 2 * out_warp_bytes(nb); }
 
-size_t smem_bytes_2d(int nb, int in_w, uint32_t bop_bytes) {
-    return 1024 /*align slack*/ + (size_t)kRawStages * raw_stage_bytes(in_w) + 2 * (size_t)out_stage_bytes(nb) +
-           bop_bytes + 8 * (2 * kRawStages + 16);
+__host__ __device__ constexpr int window_2d(int nb, bool bf) {
+    return bf ? OpFmt<true>::window(nb) : OpFmt<false>::window(nb);
+}
+
+// Banded operand bytes: every operand part of (window x N) elements.
+__host__ __device__ constexpr int bop_bytes_2d(int nb, int lines, bool bf) {
+    return (bf ? 3 * 2 : 2 * 4) * window_2d(nb, bf) * lines * nb;
+}
+
+__host__ __device__ constexpr int smem_fixed_2d(int nb, int lines, bool bf) {
+    return 1024 /*align slack*/ + out_bytes_2d(nb) + bop_bytes_2d(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16);
+}
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// TMA ring depth: as many stages (up to kMaxRawStages) as shared memory holds.
+__host__ __device__ constexpr int raw_stages_2d(int nb, int lines, bool bf) {
+    return cmin(kMaxRawStages,
+                (kSmemBudget - smem_fixed_2d(nb, lines, bf)) / raw_stage_bytes(raw_pitch(window_2d(nb, bf))));
+}
+
+__host__ __device__ constexpr int smem_bytes_2d(int nb, int lines, bool bf) {
+    return smem_fixed_2d(nb, lines, bf) + raw_stages_2d(nb, lines, bf) * raw_stage_bytes(raw_pitch(window_2d(nb, bf)));
 }
 
 // Persistent, warp-specialised sweep (R = order; NB = output columns per tile).
@@ -127,15 +155,18 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     constexpr int CW = NB / kSubs;          // epilogue columns per epilogue warp
     constexpr int GW = F::kGroup;           // input columns per split group
     constexpr int NG = K / GW;              // split groups of the input tile
-    constexpr int RSB = raw_stage_bytes(K);
-    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
+    constexpr int KP = raw_pitch(K);        // shared-memory row pitch of the raw tile
+    constexpr int RSB = raw_stage_bytes(KP);
+    constexpr int kRawStages = raw_stages_2d(NB, L, BF);
+    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
+    static_assert(kRawStages >= 3, "TMA ring too shallow");
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int OSB = out_stage_bytes(NB);
-    unsigned char* outs = smem;                               // 2 output stages (1 KB aligned)
-    unsigned char* raw = outs + 2 * OSB;                      // kRawStages tiles
+    constexpr int OWB = out_warp_bytes(NB);
+    unsigned char* outs = smem;                               // [epilogue warp][2] output buffers (1 KB aligned)
+    unsigned char* raw = outs + out_bytes_2d(NB);             // kRawStages tiles
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;                          // [kRawStages] TMA landed
@@ -145,8 +176,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     uint64_t* accf = aempty + 2;                    // [2] accumulator set ready
     uint64_t* acce = accf + 2;                      // [2] accumulator set drained
     uint64_t* bop_bar = acce + 2;
-    uint64_t* osync = bop_bar + 1;                  // epilogue warps: output-stage hand-offs
-    uint32_t* tmem_slot = (uint32_t*)(osync + 1);
+    uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int tid = threadIdx.x;
@@ -165,7 +195,6 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             ptx::mbar_init(&acce[a], kRoleWarps);
         }
         ptx::mbar_init(bop_bar, 1);
-        ptx::mbar_init(osync, kRoleWarps);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -244,7 +273,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 const int gy = Y0 + q * ROWS_OUT - R + lane;   // input row of this thread
                 const bool fix = (args.bc == kBcPeriodic) &&
                                  (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
-                const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
+                const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
                 const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
 #pragma unroll
                 for (int g0 = 0; g0 < NG; g0 += kSubs) {
@@ -311,33 +340,28 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
 #pragma unroll
                     for (int c = 0; c < CW; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[a][c]), src);
                 }
-                // Stage the outputs row-major in shared memory with the TMA
-                // swizzle (16-byte chunk index XOR row bits), then one thread
-                // writes the whole tile with a single TMA store.
-                unsigned char* ost = outs + st * OSB;
-                const bool issuer = (warp == 2 + kRoleWarps) && lane == 0;
-                if (issuer) ptx::bulk_wait_group_read<1>();   // the store that used this stage two tiles ago
-                // hand-off 1: the stage is free (bounded wait on an mbarrier, two phases per tile)
+                // Stage this warp's outputs (its CW columns of the quarter's
+                // 32 - 2R rows) row-major in its own buffer with the TMA
+                // swizzle (16-byte chunk index XOR row bits; conflict-free
+                // 16-byte stores), then write them with one TMA store.
+                unsigned char* ost = outs + ((warp - 2 - kRoleWarps) * 2 + st) * OWB;
+                if (lane == 0) ptx::bulk_wait_group_read<1>();   // this buffer's store of two tiles ago
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(osync);
-                if (!wait_or_abort(osync, 0u, abort_flag)) break;
                 if (lane >= R && lane < kSlabRows - R) {
-                    const int orow = q * ROWS_OUT + (lane - R);
+                    const int orow = lane - R;
 #pragma unroll
                     for (int c = 0; c < CW; c += 4) {
-                        const int chunk = (CW * sub + c) >> 2;
-                        const int sw = (NB == 32) ? (chunk ^ (orow & 7)) : (chunk ^ ((orow >> 1) & 3));
-                        *reinterpret_cast<float4*>(ost + orow * (NB * 4) + sw * 16) =
+                        const int chunk = c >> 2;
+                        const int sw = (CW == 16) ? (chunk ^ ((orow >> 1) & 3)) : (chunk ^ ((orow >> 2) & 1));
+                        *reinterpret_cast<float4*>(ost + orow * (CW * 4) + sw * 16) =
                             make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
                     }
                 }
                 ptx::fence_proxy_async_smem();
-                // hand-off 2: every warp's outputs are in the stage
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(osync);
-                if (!wait_or_abort(osync, 1u, abort_flag)) break;
-                if (issuer) {
-                    ptx::tma_store_2d(&tmap_out, X0, Y0, ost);
+                const int ox = X0 + CW * sub, oy = Y0 + q * ROWS_OUT;
+                if (lane == 0 && ox < args.nx && oy < args.ny) {
+                    ptx::tma_store_2d(&tmap_out, ox, oy, ost);
                     ptx::bulk_commit_group();
                 }
             }
@@ -345,7 +369,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     }
 
     // ---- teardown (also after an abort: every role has left its loop)
-    if (warp == 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
+    if (warp >= 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
     if (*abort_flag) {
         // Let copies and MMAs still in flight land before the CTA gives up its
         // shared and tensor memory (each wait bounded again).
@@ -373,31 +397,31 @@ constexpr auto kernel_for() {
 
 // ------------------------------------------------------------------ host side
 // Row-major 2D view of the grid; one box is a 32-row slab of an input tile
-// (in_w columns, in_w*4-byte TMA rows).
-bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int in_w) {
+// (pitch columns: the K window, widened to an odd number of 16-byte chunks).
+bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int pitch) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
-    cuuint32_t box[2] = {(cuuint32_t)in_w, (cuuint32_t)kSlabRows};
+    cuuint32_t box[2] = {(cuuint32_t)pitch, (cuuint32_t)kSlabRows};
     cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Row-major 2D view of the output grid; one box is a whole output tile
-// (NB columns x 4 (32-2r) rows), written from shared memory with the TMA
-// 128-byte (NB = 32) or 64-byte (NB = 16) swizzle.
-bool encode_out_map_2d(CUtensorMap* map, float* base, int ny, int nx, int nb, int rows) {
+// Row-major 2D view of the output grid; one box is one epilogue warp's share
+// of a tile (NB/2 columns x (32-2r) rows), written from shared memory with the
+// TMA 64-byte (16 columns) or 32-byte (8 columns) swizzle.
+bool encode_out_map_2d(CUtensorMap* map, float* base, int ny, int nx, int cols, int rows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
-    cuuint32_t box[2] = {(cuuint32_t)nb, (cuuint32_t)rows};
+    cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
     cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, nb == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -506,7 +530,12 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
         if (why) *why = std::string("device query: ") + cudaGetErrorString(e);
         return STENCIL_ECUDA;
     }
-    const size_t smem = smem_bytes_2d(st->nb, st->in_w, st->bop_bytes);
+    if (st->bop_bytes != (uint32_t)bop_bytes_2d(NB, L, bf)) {
+        mx_plan_free(p);
+        if (why) *why = "internal error: banded operand size";
+        return STENCIL_EUNSUPPORTED;
+    }
+    const size_t smem = smem_bytes_2d(NB, L, bf);
     e = cudaFuncSetAttribute(kernel_for_radius(q.r, bf), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         mx_plan_free(p);
@@ -557,15 +586,17 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.bpart_bytes = st->bpart_bytes;
     const int in_w = st->in_w;
     a.tiles_x = (nx + st->nb - 1) / st->nb;
-    const int tile_rows = kQuarters * (kSlabRows - 2 * p.r);
+    const int tile_rows = kQuarters * (kSlabRows - 2 * p.r);   // output rows per tile
     a.tiles_total = a.tiles_x * ((ny + tile_rows - 1) / tile_rows);
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map;
     alignas(64) CUtensorMap map_out;
-    if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, in_w)) return cudaErrorInvalidValue;
-    if (!encode_out_map_2d(&map_out, (float*)dst, ny, nx, st->nb, tile_rows)) return cudaErrorInvalidValue;
+    if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, raw_pitch(in_w))) return cudaErrorInvalidValue;
+    if (!encode_out_map_2d(&map_out, (float*)dst, ny, nx, st->nb / kSubs, kSlabRows - 2 * p.r))
+        return cudaErrorInvalidValue;
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    kernel_for_radius(p.r, st->bf)<<<grid, kThreads, smem_bytes_2d(st->nb, in_w, a.bop_bytes), s>>>(map, map_out, a);
+    const int L = 2 * p.r + 1;
+    kernel_for_radius(p.r, st->bf)<<<grid, kThreads, smem_bytes_2d(st->nb, L, st->bf), s>>>(map, map_out, a);
     return cudaGetLastError();
 }
 

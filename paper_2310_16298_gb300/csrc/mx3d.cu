@@ -42,8 +42,9 @@ constexpr int kRoleWarps = 8;
 constexpr int kSubs = 2;
 constexpr int kMathWarps = 2 * kRoleWarps;
 constexpr int kThreads = 64 + 32 * kMathWarps;
-constexpr int kRawStages = 6;
+constexpr int kMaxRawStages = 6;
 constexpr int kTmemCols = 512;
+constexpr int kSmemBudget = 227 * 1024;
 constexpr int kChunk = 32;  // output planes per work unit
 
 // Coefficient lines of a 3D stencil: (a = z offset, b = y offset) pairs that
@@ -67,12 +68,29 @@ template <bool BF>
 __host__ __device__ constexpr int tile_nb3(int L) {
     return (L * 32 <= 256 && 2 * L * 32 + 2 * a_stage_cols3<BF>(32) <= kTmemCols) ? 32 : 16;
 }
-__host__ __device__ constexpr int raw_stage_bytes3(int in_w) { return kQuarters * kSlabRows * in_w * 4; }
-__host__ __device__ constexpr int out_stage_bytes3(int nb) { return ((4 * 32 * nb * 4) + 1023) / 1024 * 1024; }
-
-size_t smem_bytes_3d(int nb, int in_w, uint32_t bop_bytes) {
-    return 1024 + (size_t)kRawStages * raw_stage_bytes3(in_w) + 2 * (size_t)out_stage_bytes3(nb) + bop_bytes +
-           8 * (2 * kRawStages + 16);
+// Raw plane slabs: K window widened to an odd number of 16-byte chunks
+// (conflict-free 16-byte row loads, as in the 2D kernel).
+__host__ __device__ constexpr int raw_pitch3(int k) { return ((k / 4) & 1) ? k : k + 4; }
+__host__ __device__ constexpr int raw_stage_bytes3(int pitch) { return kQuarters * kSlabRows * pitch * 4; }
+// Output staging: two buffers of (32 - 2r) rows x NB/2 floats per epilogue warp.
+__host__ __device__ constexpr int out_warp_bytes3(int nb) { return ((32 * (nb / kSubs) * 4) + 1023) / 1024 * 1024; }
+__host__ __device__ constexpr int out_bytes3(int nb) { return kRoleWarps * 2 * out_warp_bytes3(nb); }
+__host__ __device__ constexpr int window3(int nb, bool bf) {
+    return bf ? OpFmt<true>::window(nb) : OpFmt<false>::window(nb);
+}
+__host__ __device__ constexpr int bop_bytes3(int nb, int lines, bool bf) {
+    return (bf ? 3 * 2 : 2 * 4) * window3(nb, bf) * lines * nb;
+}
+__host__ __device__ constexpr int smem_fixed3(int nb, int lines, bool bf) {
+    return 1024 + out_bytes3(nb) + bop_bytes3(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16);
+}
+__host__ __device__ constexpr int raw_stages3(int nb, int lines, bool bf) {
+    return (kSmemBudget - smem_fixed3(nb, lines, bf)) / raw_stage_bytes3(raw_pitch3(window3(nb, bf))) < kMaxRawStages
+               ? (kSmemBudget - smem_fixed3(nb, lines, bf)) / raw_stage_bytes3(raw_pitch3(window3(nb, bf)))
+               : kMaxRawStages;
+}
+__host__ __device__ constexpr int smem_bytes_3d(int nb, int lines, bool bf) {
+    return smem_fixed3(nb, lines, bf) + raw_stages3(nb, lines, bf) * raw_stage_bytes3(raw_pitch3(window3(nb, bf)));
 }
 
 struct MxArgs3D {
@@ -102,17 +120,20 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     constexpr int PC = F::part_cols(K);
     constexpr int A_COLS = F::kMaxParts * PC;
     constexpr int CW = NB / kSubs;
-    constexpr int RSB = raw_stage_bytes3(K);
-    constexpr int OSB = out_stage_bytes3(NB);
+    constexpr int KP = raw_pitch3(K);
+    constexpr int RSB = raw_stage_bytes3(KP);
+    constexpr int kRawStages = raw_stages3(NB, L, BF);
+    constexpr int OWB = out_warp_bytes3(NB);
     constexpr int PLANES = kChunk + 2 * R;  // input planes per work unit
-    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * K * 4);
+    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
+    static_assert(kRawStages >= 3, "TMA ring too shallow");
     static_assert(N <= 256 && N % 16 == 0, "MMA N");
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* outs = smem;
-    unsigned char* raw = outs + 2 * OSB;
+    unsigned char* raw = outs + out_bytes3(NB);
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;
@@ -122,8 +143,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     uint64_t* accf = aempty + 2;
     uint64_t* acce = accf + 2;
     uint64_t* bop_bar = acce + 2;
-    uint64_t* osync = bop_bar + 1;
-    uint32_t* tmem_slot = (uint32_t*)(osync + 1);
+    uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int tid = threadIdx.x;
@@ -141,7 +161,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             ptx::mbar_init(&acce[a], kRoleWarps);
         }
         ptx::mbar_init(bop_bar, 1);
-        ptx::mbar_init(osync, kRoleWarps);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -233,7 +252,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         break;
                     }
                     ptx::tc_fence_after();
-                    const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * K;
+                    const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
                     const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
 #pragma unroll
                     for (int g0 = 0; g0 < NG; g0 += kSubs) {
@@ -261,7 +280,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 }
             }
         } else {
-            const bool issuer = (warp == 2 + kRoleWarps) && lane == 0;
             int nstore = 0;
             for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
                 int X0, Y0, Z0;
@@ -316,34 +334,26 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&acce[st]);
                     if (iz >= 2 * R) {
-                        // output plane Z0 + iz - 2R is complete: stage it and store it
-                        unsigned char* ost = outs + (nstore & 1) * OSB;
-                        if (issuer) ptx::bulk_wait_group_read<1>();
+                        // output plane Z0 + iz - 2R is complete: this warp stages its
+                        // share (swizzled, conflict-free) and stores it with one TMA store
+                        unsigned char* ost = outs + ((warp - 2 - kRoleWarps) * 2 + (nstore & 1)) * OWB;
+                        if (lane == 0) ptx::bulk_wait_group_read<1>();
                         __syncwarp();
-                        if (lane == 0) ptx::mbar_arrive(osync);
-                        if (!wait_or_abort(osync, 0u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
                         if (lane >= R && lane < kSlabRows - R) {
-                            const int orow = q * ROWS_OUT + (lane - R);
+                            const int orow = lane - R;
 #pragma unroll
                             for (int c = 0; c < CW; c += 4) {
-                                const int chunk = (CW * sub + c) >> 2;
-                                const int sw = (NB == 32) ? (chunk ^ (orow & 7)) : (chunk ^ ((orow >> 1) & 3));
-                                *reinterpret_cast<float4*>(ost + orow * (NB * 4) + sw * 16) =
+                                const int chunk = c >> 2;
+                                const int sw = (CW == 16) ? (chunk ^ ((orow >> 1) & 3)) : (chunk ^ ((orow >> 2) & 1));
+                                *reinterpret_cast<float4*>(ost + orow * (CW * 4) + sw * 16) =
                                     make_float4(acc[0][c], acc[0][c + 1], acc[0][c + 2], acc[0][c + 3]);
                             }
                         }
                         ptx::fence_proxy_async_smem();
                         __syncwarp();
-                        if (lane == 0) ptx::mbar_arrive(osync);
-                        if (!wait_or_abort(osync, 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        if (issuer) {
-                            ptx::tma_store_3d(&tmap_out, X0, Y0, Z0 + iz - 2 * R, ost);
+                        const int ox = X0 + CW * sub, oy = Y0 + q * ROWS_OUT;
+                        if (lane == 0 && ox < args.nx && oy < args.ny && Z0 + iz - 2 * R < args.nz) {
+                            ptx::tma_store_3d(&tmap_out, ox, oy, Z0 + iz - 2 * R, ost);
                             ptx::bulk_commit_group();
                         }
                         ++nstore;
@@ -360,7 +370,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         }
     }
 
-    if (warp == 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();
+    if (warp >= 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();
     if (*abort_flag) {
         if (warp == 0 && lane == 0) {
             for (int k = issued - kRawStages; k < issued; ++k)
@@ -409,27 +419,28 @@ int line3_b(int r, bool star, int l) {
     return star ? (l < r || l >= r + W ? r : l - r) : l % W;
 }
 
-bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int nx, int in_w) {
+bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int nx, int pitch) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)in_w, (cuuint32_t)kSlabRows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)pitch, (cuuint32_t)kSlabRows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, int nb, int rows) {
+// One box = one epilogue warp's share of an output plane tile (cols = NB/2).
+bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, int cols, int rows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)nb, (cuuint32_t)rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, nb == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -505,9 +516,10 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && st->bop_bytes != (uint32_t)bop_bytes3(NB, L, bf)) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel3_for(r, q.star, bf), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes_3d(NB, KW, st->bop_bytes));
+                                 smem_bytes_3d(NB, L, bf));
     p->tmap_storage = st;
     if (e != cudaSuccess) {
         if (why) *why = std::string("3D plan set-up: ") + cudaGetErrorString(e);
@@ -557,11 +569,12 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     a.units = a.tiles_x * a.tiles_y * a.chunks;
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map, map_out;
-    if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, in_w)) return cudaErrorInvalidValue;
-    if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb, rows_tile)) return cudaErrorInvalidValue;
+    if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, raw_pitch3(in_w))) return cudaErrorInvalidValue;
+    if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb / kSubs, kSlabRows - 2 * p.r))
+        return cudaErrorInvalidValue;
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
-    kernel3_for(p.r, st->star, st->bf)<<<grid, kThreads, smem_bytes_3d(st->nb, in_w, a.bop_bytes), s>>>(map, map_out,
-                                                                                                     a);
+    const int smem = smem_bytes_3d(st->nb, lines3(p.r, st->star), st->bf);
+    kernel3_for(p.r, st->star, st->bf)<<<grid, kThreads, smem, s>>>(map, map_out, a);
     return cudaGetLastError();
 }
 
