@@ -22,7 +22,11 @@ import subprocess
 import sys
 import time
 
+import dataclasses
+
 import numpy as np
+
+from paper_2310_16298_gb300 import replicas
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -245,7 +249,9 @@ def run_batch_workload(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    probs = si.batch_1024(args.batch)
+    # the batch of every rank is its shard of world x n problems (independent units)
+    allp = si.batch_1024(args.batch * world)
+    probs = [allp[i] for i in replicas.shard(len(allp), rank, world)]
     plans, xs, ys = [], [], []
     for p in probs:
         plans.append(sx.stencil_plan_create(p.shape, p.r, p.kind, p.coeffs, "f32",
@@ -276,11 +282,8 @@ def run_batch_workload(args):
     clk = sampler.stop()
     ms = [a.elapsed_time(e) for a, e in ev]
     tot = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = float(t.item())
-    value = info["updates"] * args.steps * world / tot / 1e9
+    tot = replicas.max_over_ranks(tot, dev)
+    value = replicas.sum_over_ranks(info["updates"] * args.steps, dev) / tot / 1e9
     # accuracy: a few problems against the oracle at sampled points
     import oracle
     errs = []
@@ -310,6 +313,8 @@ def run_batch_workload(args):
     sx.stencil_batch_destroy(b)
     for p in plans:
         sx.stencil_plan_destroy(p)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 # ------------------------------------------------------------------ serving workload
@@ -326,7 +331,13 @@ def run_serving_workload(args):
     import stencil_inputs as si
     torch.cuda.set_device(local)
     n = args.batch if args.batch != 1024 else 2000
-    base = si.serving_stream(n, rate_per_s=1.0)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    # every rank serves the requests a round-robin router sends it from a
+    # stream of world x n requests (independent units, no data exchange)
+    base = replicas.routed(si.serving_stream(n * world, rate_per_s=1.0), rank, world)
 
     def serve(arrivals):
         srv = sx.stencil_server_create(120 * 10**9, 64, 16, 8)
@@ -356,15 +367,19 @@ def run_serving_workload(args):
     sampler = ClockSampler(local)
     sampler.start()
     lat_s, upd, span, st_s = serve([(0.0, q) for q in base])
-    sat_rate = n / span
-    results = {"saturated": {"requests_per_s": sat_rate, "gstencil_s": upd / span / 1e9, "makespan_s": span,
+    sat_rate = n / span   # this rank's saturated rate
+    span_all = replicas.max_over_ranks(span, dev)
+    results = {"saturated": {"requests_per_s": replicas.sum_over_ranks(n, dev) / span_all,
+                             "gstencil_s": replicas.sum_over_ranks(upd, dev) / span_all / 1e9, "makespan_s": span_all,
                              "p50_latency_s": float(np.percentile(lat_s, 50)),
                              "p99_latency_s": float(np.percentile(lat_s, 99)), "peak_resident": st_s["peak_resident"],
                              "peak_bytes": st_s["peak_bytes"]}}
     for frac in (0.5, 0.8):
-        stream = si.serving_stream(n, rate_per_s=frac * sat_rate)
+        stream = replicas.routed(si.serving_stream(n * world, rate_per_s=frac * sat_rate * world), rank, world)
         lat, upd_f, span_f, st_f = serve([(q.arrival_s, q) for q in stream])
-        results[f"load_{frac}"] = {"offered_requests_per_s": frac * sat_rate, "gstencil_s": upd_f / span_f / 1e9,
+        span_f = replicas.max_over_ranks(span_f, dev)
+        results[f"load_{frac}"] = {"offered_requests_per_s": replicas.sum_over_ranks(frac * sat_rate, dev),
+                                   "gstencil_s": replicas.sum_over_ranks(upd_f, dev) / span_f / 1e9,
                                    "p50_latency_s": float(np.percentile(lat, 50)),
                                    "p99_latency_s": float(np.percentile(lat, 99)),
                                    "peak_resident": st_f["peak_resident"], "peak_bytes": st_f["peak_bytes"]}
@@ -372,7 +387,7 @@ def run_serving_workload(args):
     if rank == 0:
         head = results["load_0.8"]
         line = {"metric": METRIC, "value": head["gstencil_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
-                "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
+                "warmup": 0, "ms_per_step": span_all * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"serving: {n} Poisson-arrival requests, 70% 2D (128^2..4096^2, r 1..3, "
                                        f"star|box), 30% 3D (64^3..384^3, 7/27-point), FP32 with 10% FP64, steps "
@@ -382,6 +397,8 @@ def run_serving_workload(args):
                 "p50_ms": head["p50_latency_s"] * 1e3, "p99_ms": head["p99_latency_s"] * 1e3,
                 "serving": results, "clocks": clk}
         print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 # ------------------------------------------------------------------ our arm
@@ -404,6 +421,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     p = workload(args)
+    if world > 1:   # every rank solves its own independent grid (a replica with its own field)
+        p = dataclasses.replace(p, field_seed=replicas.field_seed(p.field_seed, rank))
     field = p.field()
     td = torch.float32 if p.dtype == "f32" else torch.float64
     x = torch.tensor(field, dtype=td, device=dev)
@@ -470,12 +489,8 @@ def main():
     sampler = ClockSampler(local)
     ms, t_host, clk = time_solves(plan, args.steps, args.warmup, sampler)
     tot = float(np.sum(ms)) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    updates = p.updates * args.steps * world
+    tot = replicas.max_over_ranks(tot, dev)
+    updates = replicas.sum_over_ranks(p.updates * args.steps, dev)
     value = updates / tot / 1e9
     per_solve = np.array(ms)
     results[main_impl]["timing"] = ms
@@ -518,7 +533,8 @@ def main():
             t0 = time.perf_counter()
             sx.stencil_apply_host(plan.handle, h_in.numpy(), h_out.numpy(), p.steps)
             et.append(time.perf_counter() - t0)
-        e2e = {"value": p.updates / float(np.median(et)) / 1e9 * world, "unit": UNIT,
+        e2e_t = replicas.max_over_ranks(float(np.median(et)), dev)
+        e2e = {"value": replicas.sum_over_ranks(p.updates, dev) / e2e_t / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
                "api": "stencil_apply_host (pinned host buffers, H2D + solve + D2H)"}
@@ -547,7 +563,7 @@ def main():
                                                     "parallelism": f"replicas x{world}"}),
                 "p50_ms": float(np.percentile(per_solve, 50)), "p99_ms": float(np.percentile(per_solve, 99)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_solve * args.steps, "clocks": clk, "compare": comp,
+                "gpu_launches": launches_per_solve * args.steps * world, "clocks": clk, "compare": comp,
                 "host_s": t_host}
         print(json.dumps(line), flush=True)
     for res in results.values():

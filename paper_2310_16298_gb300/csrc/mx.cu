@@ -1,45 +1,67 @@
-// Matrixized stencil sweep on the 5th-generation tensor cores (tcgen05).
+// Matrixized 2D stencil sweep on the 5th-generation tensor cores (tcgen05).
 //
 // Scatter-mode formulation (Sec. 3): every coefficient line contributes, to
 // an output block, the sum over its input vectors of (input vector) x
-// (coefficient vector) outer products -- Eq. (final).  The kernels take the
-// lines along the contiguous axis (the paper's orthogonal line orientation,
-// Eq. (to-outer-product-2-star)), so for line a (input row offset a - r) and
-// an output block of Nb columns
+// (coefficient vector) outer products -- Eq. (final).  The lines run along
+// the contiguous axis x (the orientation of Eq. (to-outer-product-2-star)):
+// line a holds row a of C^g, i.e. the weights of input row offset a - r.  For
+// an output block of NB = 16 columns starting at X0, line a applied to input
+// row y is the product of the row's K window (columns X0-4 .. X0-4+W-1) with
+// the line's banded Toeplitz operand
 //
-//     D[m, q] += sum_k A[m + a, k] * H_a[k, q],   H_a[k, q] = C^g[a, k - q - 4 + r]
+//     H_a[k, q] = C^g[a, k - q - 4 + r],
 //
-// where A is the K = Nb + 8 column window of the input tile starting 4
-// columns left of the block and H_a is the line's banded (Toeplitz) operand:
-// the columns of H_a are the coefficient vectors of Eq. (co) / Eq. (final).
-// One tcgen05.mma (M = 128 rows, N = Nb, K = 8) sums 8 such outer products;
-// the accumulator D stays in tensor memory for the whole sweep of the tile.
+// whose columns are the coefficient vectors (windows of a column of C^o,
+// Eq. (co)).  One tcgen05.mma (M = 128, N, K = 8 or 16) sums K such outer
+// products for 128 rows at once; the accumulators stay in tensor memory.
 //
-// Shared-memory layout of the input tile ("slabs", K-major, no swizzle):
-// slab s holds columns 4s..4s+3 of every tile row, one 16-byte row after the
-// other.  This is the tcgen05 canonical no-swizzle layout with SBO = 128 B
-// (8 rows) and LBO = slab size, so the operand for line a is the same
-// descriptor moved by a*16 bytes: the row shift every coefficient line needs
-// costs nothing (the paper's data-alignment conflict, Sec. 4.3, does not
-// arise).  TMA brings each tile in row-major (160-byte box rows); the pass
-// that splits it into TF32 parts also transposes it into slabs.
+// Row pairs.  The line sum needs, for output row Y, the partials of line a
+// at input row Y + a - r: a shift across the accumulator rows (TMEM lanes),
+// which only warp shuffles can apply.  To halve those shuffles every TMEM
+// lane m holds two input rows, 2m (even) and 2m+1 (odd), side by side along
+// K (K = 2W), and the B operand is made of 2r+2 column blocks, block (p, d)
+// stacking H_{a0} over H_{a0+1} with a0 = 2d - p + r (lines outside 0..2r
+// are zero).  Lane m+d of block (p, d) then holds exactly the contribution
+// of its two rows to output row 2m+p, so
 //
-// Precision: TF32 (one product) or TF32x3 (a = a_hi + a_lo, h = h_hi + h_lo,
-// products lo*hi + hi*lo + hi*hi accumulated in FP32), split in shared memory
-// once per tile.
+//     B[2m + p, :] = sum_d D[m + d, block (p, d)],     |d| <= ceil(r/2),
+//
+// r shuffles per output instead of 2r, and fewer MACs per output than one
+// lane per row.
+//
+// Roles (one persistent CTA per SM, warp specialised):
+//  * warp 0: TMA producer.  A tile is 4 lane quarters x 64 input rows; each
+//    quarter is loaded as two 32-row boxes through row-parity tensor maps
+//    (even rows, odd rows), so a warp reads consecutive rows (no bank
+//    conflicts) and every lane's two rows sit in the same smem slot.
+//  * warp 1: MMA issuer (one elected thread).
+//  * warps 2..9: split warps, one per (quarter, row parity): input rows ->
+//    TF32 hi/lo (or BF16 parts) -> tensor memory (tcgen05.st).
+//  * warps 10..17: epilogue warps, one per (quarter, output parity): tensor
+//    memory -> shuffles -> swizzled smem -> TMA store through the output
+//    row-parity tensor map.
+// Two or three A stages (as many as tensor memory holds beside two
+// accumulator sets) overlap split, MMA and epilogue; every wait is bounded
+// (a timeout sets a host-visible error word, drains copies in flight and
+// frees tensor memory).
+//
+// Precision: TF32, TF32x3, BF16, BF16x2, BF16x3 (operand parts products
+// accumulated smallest first in FP32; the epilogue sums the blocks in FP32
+// round-to-nearest).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <array>
 #include <cmath>
-#include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "mx.h"
+#include "mxutil.cuh"
 #include "plan.h"
 #include "ptx.cuh"
-#include "mxutil.cuh"
 
 namespace stx {
 
@@ -47,133 +69,113 @@ namespace {
 
 using namespace mxu;
 
-constexpr int kPad = 4;                 // input columns left/right of the output columns
-constexpr int kSlabRows = 32;           // input rows per warp slab (= TMEM lanes of one warp)
-constexpr int kQuarters = 4;            // TMEM lane quarters = warp slabs per tile
-constexpr int kMathWarps = 16;          // 8 split warps + 8 epilogue warps
-constexpr int kRoleWarps = 8;           // warps per role: two per lane quarter
-constexpr int kSubs = 2;                // warps of one role per lane quarter
-constexpr int kThreads = 64 + 32 * kMathWarps;  // producer warp, MMA warp, math warps
-constexpr int kMathThreads = 32 * kMathWarps;
-constexpr int kMaxRawStages = 6;        // TMA ring depth (fewer where shared memory runs out)
+constexpr int kPad = 4;                 // input columns left of the output block
+constexpr int kLanes = 32;              // TMEM lanes per warp (lane quarter)
+constexpr int kQuarters = 4;
+constexpr int kNb = 16;                 // output columns per tile
+constexpr int kSplitWarps = 2 * kQuarters;   // (quarter, input row parity)
+constexpr int kEpiWarps = 2 * kQuarters;     // (quarter, output row parity)
+constexpr int kThreads = 64 + 32 * (kSplitWarps + kEpiWarps);
+constexpr int kMaxRawStages = 6;
 constexpr int kTmemCols = 512;
 constexpr int kSmemBudget = 227 * 1024;
 
-// Output columns per tile (the MMA block width) for a stencil with L lines:
-// 32 while both accumulator sets (2 x L x 32 columns) and both A stages fit
-// the 512 TMEM columns, else 16.
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// Row-pair geometry of order R.
+template <int R>
+struct Pair {
+    static constexpr int DM = (R + 1) / 2;              // lanes an output row reaches on either side
+    static constexpr int LANES_OUT = kLanes - 2 * DM;   // lanes of a quarter that produce outputs
+    static constexpr int ROWS_OUT = 2 * LANES_OUT;      // output rows per quarter
+    static constexpr int NBP = R + 1;                   // blocks per output parity
+    static constexpr int NBLK = 2 * NBP;
+    // lane offset d of block (p, i) is dlo(p) + i
+    __host__ __device__ static constexpr int dlo(int p) { return -((R + 1 - p) / 2); }
+};
+
 template <bool BF>
-__host__ __device__ constexpr int a_stage_cols(int nb) {
-    return OpFmt<BF>::kMaxParts * OpFmt<BF>::part_cols(OpFmt<BF>::window(nb));
+__host__ __device__ constexpr int window(int nb) { return BF ? OpFmt<true>::window(nb) : OpFmt<false>::window(nb); }
+
+// Shared-memory row pitch of the raw tile: the window widened to an odd
+// number of 16-byte chunks (eight consecutive rows = eight bank groups).
+__host__ __device__ constexpr int raw_pitch(int w) { return ((w / 4) & 1) ? w : w + 4; }
+template <bool BF>
+__host__ __device__ constexpr int raw_stage_bytes() { return 2 * kQuarters * kLanes * raw_pitch(window<BF>(kNb)) * 4; }
+
+// Output staging: two buffers per epilogue warp of (32 - 2 DM) rows x 16 floats.
+__host__ __device__ constexpr int out_warp_bytes() { return 2048; }
+__host__ __device__ constexpr int out_bytes() { return kEpiWarps * 2 * out_warp_bytes(); }
+
+template <int R, bool BF>
+__host__ __device__ constexpr int bop_bytes() {
+    return (BF ? 3 * 2 : 2 * 4) * 2 * window<BF>(kNb) * Pair<R>::NBLK * kNb;
 }
-template <bool BF>
-__host__ __device__ constexpr int tile_nb(int L) { return (2 * L * 32 + 2 * a_stage_cols<BF>(32) <= kTmemCols) ? 32 : 16; }
+template <int R, bool BF>
+__host__ __device__ constexpr int smem_fixed() {
+    return 1024 /*align slack*/ + out_bytes() + bop_bytes<R, BF>() + 8 * (2 * kMaxRawStages + 16);
+}
+template <int R, bool BF>
+__host__ __device__ constexpr int raw_stages() {
+    return cmin(kMaxRawStages, (kSmemBudget - smem_fixed<R, BF>()) / raw_stage_bytes<BF>());
+}
+template <int R, bool BF>
+__host__ __device__ constexpr int smem_bytes() {
+    return smem_fixed<R, BF>() + raw_stages<R, BF>() * raw_stage_bytes<BF>();
+}
 
 struct MxArgs2D {
-    float* out;
-    const float* in;          // source grid (periodic halo fix-up reads it directly)
-    const void* bops;         // banded operands [part][kchunk][line*NB + q][16 bytes]
-    unsigned int* err;        // device error word (host-mapped)
+    const float* in;           // source grid (periodic halo fix-up reads it directly)
+    const void* bops;          // block operands [part][kchunk][block*16 + q][16 bytes]
+    unsigned int* err;         // device error word (host-mapped)
     int ny, nx;
     int bc, nparts;            // operand parts of the input split (1..3)
     int tiles_x, tiles_total;
+    int rows_even, rows_odd;   // rows of the even / odd row-parity views
     uint32_t bop_bytes;        // every part
     uint32_t bpart_bytes;      // one part
     int nprod;                 // products per K step (1, 3 or 6)
 };
 
-// Shared-memory row pitch of the raw input tile: the K window widened to an
-// odd number of 16-byte chunks, so that the 16-byte loads of eight
-// consecutive rows (one shared-memory wavefront) fall in eight distinct bank
-// groups.  The extra columns are loaded by TMA and never read.
-__host__ __device__ constexpr int raw_pitch(int k) { return ((k / 4) & 1) ? k : k + 4; }
-__host__ __device__ constexpr int raw_stage_bytes(int pitch) { return kQuarters * kSlabRows * pitch * 4; }
-
-// Output staging: every epilogue warp owns two buffers of (32 - 2r) rows x
-// NB/2 floats (its share of the tile), each padded to 1 KB, and writes them
-// with its own TMA store.
-__host__ __device__ constexpr int out_warp_bytes(int nb) { return ((32 * (nb / kSubs) * 4) + 1023) / 1024 * 1024; }
-__host__ __device__ constexpr int out_bytes_2d(int nb) { return kRoleWarps * 2 * out_warp_bytes(nb); }
-
-__host__ __device__ constexpr int window_2d(int nb, bool bf) {
-    return bf ? OpFmt<true>::window(nb) : OpFmt<false>::window(nb);
-}
-
-// Banded operand bytes: every operand part of (window x N) elements.
-__host__ __device__ constexpr int bop_bytes_2d(int nb, int lines, bool bf) {
-    return (bf ? 3 * 2 : 2 * 4) * window_2d(nb, bf) * lines * nb;
-}
-
-__host__ __device__ constexpr int smem_fixed_2d(int nb, int lines, bool bf) {
-    return 1024 /*align slack*/ + out_bytes_2d(nb) + bop_bytes_2d(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16);
-}
-
-__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
-
-// TMA ring depth: as many stages (up to kMaxRawStages) as shared memory holds.
-__host__ __device__ constexpr int raw_stages_2d(int nb, int lines, bool bf) {
-    return cmin(kMaxRawStages,
-                (kSmemBudget - smem_fixed_2d(nb, lines, bf)) / raw_stage_bytes(raw_pitch(window_2d(nb, bf))));
-}
-
-__host__ __device__ constexpr int smem_bytes_2d(int nb, int lines, bool bf) {
-    return smem_fixed_2d(nb, lines, bf) + raw_stages_2d(nb, lines, bf) * raw_stage_bytes(raw_pitch(window_2d(nb, bf)));
-}
-
-// Persistent, warp-specialised sweep (R = order; NB = output columns per tile).
-//  * Warp 0 streams input tiles with TMA into a ring of shared-memory buffers.
-//    A tile is four overlapping 32-row slabs (one per TMEM lane quarter) of
-//    NB + 8 columns; slab q covers input rows Y0 + q*(32-2R) - R + [0, 32).
-//  * Warps 2..9 (two per lane quarter) split their slab into TF32 hi and lo
-//    parts and write them straight into tensor memory (tcgen05.st): the A
-//    operand never goes back through shared memory.
-//  * Warps 10..17 (two per lane quarter) drain finished accumulators and write
-//    the outputs, concurrently with the split of later tiles.
-//  * Warp 1 issues the outer products.  All 2R+1 coefficient lines of the
-//    stencil sit side by side along N (B = [H_0 | ... | H_2R], N = NB (2R+1)),
-//    so one tcgen05.mma applies every line to the same input rows; line a's
-//    partial sums land in columns a*NB .. a*NB+NB-1.  The row shift a - R of
-//    each line is applied in the epilogue with warp shuffles, which is why
-//    each 32-row warp slab yields 32 - 2R output rows.
-//  * Accuracy: TF32x3 products are accumulated corrections first (lo*hi,
-//    hi*lo) and the large hi*hi products last, so each line accumulator sees
-//    only (NB+8)/8 large additions (the tensor core's FP32 accumulation
-//    truncates); the lines are summed in FP32 round-to-nearest in the
-//    epilogue.
-template <int R, int NB, bool BF>
+template <int R, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
-mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
+mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ CUtensorMap tmap_o,
+            const __grid_constant__ CUtensorMap omap_e, const __grid_constant__ CUtensorMap omap_o,
             const MxArgs2D args) {
     using F = OpFmt<BF>;
-    constexpr int L = 2 * R + 1;            // lines
-    constexpr int N = L * NB;               // MMA N
-    constexpr int K = F::window(NB);        // input columns per tile = K window
-    constexpr int KS = K / F::kKStep;       // MMAs per window and product
-    constexpr int ROWS_OUT = kSlabRows - 2 * R;
-    constexpr int PC = F::part_cols(K);     // TMEM columns of one operand part
-    constexpr int A_COLS = F::kMaxParts * PC;  // TMEM columns of one A stage
-    constexpr int CW = NB / kSubs;          // epilogue columns per epilogue warp
+    using G = Pair<R>;
+    constexpr int N = G::NBLK * kNb;        // MMA N
+    constexpr int W = window<BF>(kNb);      // K window of one input row
+    constexpr int KW = 2 * W;               // K: even-row window | odd-row window
+    constexpr int KS = KW / F::kKStep;      // MMAs per product
+    constexpr int PC = F::part_cols(KW);    // TMEM columns of one operand part
+    constexpr int A_COLS = F::kMaxParts * PC;
     constexpr int GW = F::kGroup;           // input columns per split group
-    constexpr int NG = K / GW;              // split groups of the input tile
-    constexpr int KP = raw_pitch(K);        // shared-memory row pitch of the raw tile
-    constexpr int RSB = raw_stage_bytes(KP);
-    constexpr int kRawStages = raw_stages_2d(NB, L, BF);
-    constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
+    constexpr int NG = W / GW;              // split groups per row
+    constexpr int WU = kNb + 2 * kPad;      // window columns that carry weights
+    constexpr int KP = raw_pitch(W);
+    constexpr int SLAB = kLanes * KP * 4;   // one (parity, quarter) box
+    constexpr int RSB = raw_stage_bytes<BF>();
+    constexpr int kRawStages = raw_stages<R, BF>();
+    constexpr int OWB = out_warp_bytes();
+    constexpr int AST = (3 * A_COLS + 2 * N <= kTmemCols) ? 3 : 2;   // A operand stages in TMEM
     static_assert(kRawStages >= 3, "TMA ring too shallow");
+    static_assert(N % 16 == 0 && N <= 256, "MMA N");
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
+    static_assert(2 * kRawStages + 2 * AST + 5 <= 2 * kMaxRawStages + 15, "barrier space");
+    static_assert(G::LANES_OUT * kNb * 4 <= OWB, "output staging");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int OWB = out_warp_bytes(NB);
-    unsigned char* outs = smem;                               // [epilogue warp][2] output buffers (1 KB aligned)
-    unsigned char* raw = outs + out_bytes_2d(NB);             // kRawStages tiles
+    unsigned char* outs = smem;                     // [epilogue warp][2] output buffers (1 KB aligned)
+    unsigned char* raw = outs + out_bytes();        // [stage][parity][quarter] 32-row boxes
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;                          // [kRawStages] TMA landed
-    uint64_t* rawfree = bars + kRawStages;          // [kRawStages] slab read by its math warps
-    uint64_t* afull = bars + 2 * kRawStages;        // [2] A operand stage written to TMEM
-    uint64_t* aempty = afull + 2;                   // [2] MMAs done reading the A stage
-    uint64_t* accf = aempty + 2;                    // [2] accumulator set ready
+    uint64_t* rawfree = bars + kRawStages;          // [kRawStages] rows read by the split warps
+    uint64_t* afull = bars + 2 * kRawStages;        // [AST] A operand stage written to TMEM
+    uint64_t* aempty = afull + AST;                 // [AST] MMAs done reading the A stage
+    uint64_t* accf = aempty + AST;                  // [2] accumulator set ready
     uint64_t* acce = accf + 2;                      // [2] accumulator set drained
     uint64_t* bop_bar = acce + 2;
     uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
@@ -183,16 +185,17 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     const int warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        // split/epilogue barriers count one (elected) arrival per warp of the role
         for (int s = 0; s < kRawStages; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&rawfree[s], kRoleWarps);
+            ptx::mbar_init(&rawfree[s], kSplitWarps);
+        }
+        for (int a = 0; a < AST; ++a) {
+            ptx::mbar_init(&afull[a], kSplitWarps);
+            ptx::mbar_init(&aempty[a], 1);
         }
         for (int a = 0; a < 2; ++a) {
-            ptx::mbar_init(&afull[a], kRoleWarps);
-            ptx::mbar_init(&aempty[a], 1);
             ptx::mbar_init(&accf[a], 1);
-            ptx::mbar_init(&acce[a], kRoleWarps);
+            ptx::mbar_init(&acce[a], kEpiWarps);
         }
         ptx::mbar_init(bop_bar, 1);
         *abort_flag = 0;
@@ -206,8 +209,8 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tmem_a = tmem;                          // A stages: [2][hi | lo]
-    const uint32_t tmem_d = tmem + (uint32_t)(2 * A_COLS);  // accumulator sets: [2][N]
+    const uint32_t tmem_a = tmem;                             // A stages: [AST][parts]
+    const uint32_t tmem_d = tmem + (uint32_t)(AST * A_COLS);  // accumulator sets: [2][N]
     int issued = 0;        // producer: TMA tiles issued
     int committed = -1;    // MMA issuer: last tile whose MMAs were committed
 
@@ -221,13 +224,17 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
                 if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag)) break;
-                const int X0 = (t % args.tiles_x) * NB;
-                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
+                const int X0 = (t % args.tiles_x) * kNb;
+                const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
                 unsigned char* dst = raw + s * RSB;
-                ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
+                ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)RSB);
 #pragma unroll
-                for (int q = 0; q < kQuarters; ++q)
-                    ptx::tma_load_2d(dst + q * SLAB_BOX, &tmap, X0 - kPad, Y0 + q * ROWS_OUT - R, &full[s]);
+                for (int q = 0; q < kQuarters; ++q) {
+                    // quarter q covers input rows Y0 + q*ROWS_OUT - 2*DM + [0, 64): an even start
+                    const int yp = (Y0 + q * G::ROWS_OUT - 2 * G::DM) / 2;   // row in the parity views
+                    ptx::tma_load_2d(dst + q * SLAB, &tmap_e, X0 - kPad, yp, &full[s]);
+                    ptx::tma_load_2d(dst + (kQuarters + q) * SLAB, &tmap_o, X0 - kPad, yp, &full[s]);
+                }
                 issued = i + 1;
             }
         }
@@ -239,137 +246,156 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             const int pr = args.nprod;
             int i = 0;
             for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+                const int sa = i % AST;
+                const uint32_t pa = (uint32_t)(i / AST) & 1u;
                 const int st = i & 1;
                 const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                if (!wait_or_abort(&afull[st], ph, abort_flag)) break;
+                if (!wait_or_abort(&afull[sa], pa, abort_flag)) break;
                 if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
                 ptx::tc_fence_after();
-                issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(st * A_COLS), PC, b0,
+                issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
                                        args.bpart_bytes, N, idesc, pr);
-                ptx::mma_commit(&aempty[st]);
+                ptx::mma_commit(&aempty[sa]);
                 ptx::mma_commit(&accf[st]);
                 committed = i;
             }
         }
-    } else {
-        // ------------------------------------------------ math warps
-        const int q = warp & 3;                        // TMEM lane quarter (= warp slab) of this warp
-        const bool split_role = (warp - 2) < kRoleWarps;
-        const int sub = ((warp - 2) >> 2) & 1;         // which half of the role's work this warp takes
+    } else if (warp < 2 + kSplitWarps) {
+        // ------------------------------------------------ split: rows (smem) -> operand parts (TMEM)
+        const int q = warp & 3;                        // TMEM lane quarter of this warp
+        const int e = (warp - 2) >> 2;                 // input row parity this warp converts
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        if (split_role) {
-            // ---------------- split: raw tile (smem) -> TF32 hi/lo A operand (TMEM)
-            int i = 0;
-            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
-                const int rs = i % kRawStages;
-                const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
-                const int st = i & 1;
-                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[st], ph ^ 1u, abort_flag))
-                    break;
-                ptx::tc_fence_after();
-                const int X0 = (t % args.tiles_x) * NB;
-                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
-                const int gy = Y0 + q * ROWS_OUT - R + lane;   // input row of this thread
-                const bool fix = (args.bc == kBcPeriodic) &&
-                                 (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + K > args.nx);
-                const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
-                const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
+        int i = 0;
+        for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+            const int rs = i % kRawStages;
+            const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
+            const int sa = i % AST;
+            const uint32_t pa = (uint32_t)(i / AST) & 1u;
+            if (!wait_or_abort(&full[rs], rph, abort_flag)) break;
+            const int X0 = (t % args.tiles_x) * kNb;
+            const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
+            const int gy = Y0 + q * G::ROWS_OUT - 2 * G::DM + 2 * lane + e;   // input row of this thread
+            const bool fix = (args.bc == kBcPeriodic) &&
+                             (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + WU > args.nx);
+            const float* row =
+                reinterpret_cast<const float*>(raw + rs * RSB + (e * kQuarters + q) * SLAB) + (size_t)lane * KP;
+            float x[NG][GW];
 #pragma unroll
-                for (int g0 = 0; g0 < NG; g0 += kSubs) {
-                    const int g = g0 + sub;
-                    if (g >= NG) break;
-                    const int c0 = GW * g;
-                    float x[GW];
+            for (int g = 0; g < NG; ++g) {
 #pragma unroll
-                    for (int c4 = 0; c4 < GW; c4 += 4) {
-                        float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
-                        if (fix) {
-                            const int gx = X0 - kPad + c0 + c4;
-                            if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
-                                v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
-                                                                     wrap_index(gx, args.nx));
-                        }
-                        x[c4] = v.x;
-                        x[c4 + 1] = v.y;
-                        x[c4 + 2] = v.z;
-                        x[c4 + 3] = v.w;
+                for (int c4 = 0; c4 < GW; c4 += 4) {
+                    float4 v = *reinterpret_cast<const float4*>(row + GW * g + c4);
+                    if (fix) {
+                        const int gx = X0 - kPad + GW * g + c4;
+                        if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
+                            v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
+                                                                 wrap_index(gx, args.nx));
                     }
-                    split_store<BF>(x, abase, PC, c0, args.nparts);
-                }
-                ptx::tmem_wait_st();
-                ptx::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    ptx::mbar_arrive(&rawfree[rs]);
-                    ptx::mbar_arrive(&afull[st]);
+                    x[g][c4] = v.x;
+                    x[g][c4 + 1] = v.y;
+                    x[g][c4 + 2] = v.z;
+                    x[g][c4 + 3] = v.w;
                 }
             }
-        } else {
-            // ---------------- epilogue: accumulators (TMEM) -> row shifts -> outputs (global)
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&rawfree[rs]);   // the rows are in registers
+            if (!wait_or_abort(&aempty[sa], pa ^ 1u, abort_flag)) break;
+            ptx::tc_fence_after();
+            const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) split_store<BF>(x[g], abase, PC, e * W + GW * g, args.nparts);
+            ptx::tmem_wait_st();
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&afull[sa]);
+        }
+    } else {
+        // ------------------------------------------------ epilogue: accumulators -> outputs
+        const int q = warp & 3;
+        const int p = (warp - 2 - kSplitWarps) >> 2;   // output row parity of this warp
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        unsigned char* obuf = outs + (warp - 2 - kSplitWarps) * 2 * OWB;
+        auto drain = [&](auto pc) {
+            constexpr int P = decltype(pc)::value;
+            constexpr int DLO = G::dlo(P);
+            constexpr int I0 = -DLO;                          // the block with lane offset 0
+            constexpr int LB = G::NBP <= 3 ? G::NBP : 2;      // blocks per TMEM load batch
+            const CUtensorMap* omap = P ? &omap_o : &omap_e;
+            const int prows = P ? args.rows_odd : args.rows_even;
             int i = 0;
             for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
                 const int st = i & 1;
                 const uint32_t ph = (uint32_t)(i >> 1) & 1u;
                 if (!wait_or_abort(&accf[st], ph, abort_flag)) break;
                 ptx::tc_fence_after();
-                const int X0 = (t % args.tiles_x) * NB;
-                const int Y0 = (t / args.tiles_x) * (kQuarters * ROWS_OUT);
-                // this warp's CW of the tile's NB columns, for every line
-                const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + CW * sub);
-                uint32_t v[L][CW];
+                const int X0 = (t % args.tiles_x) * kNb;
+                const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
+                const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + P * G::NBP * kNb);
+                float acc[kNb];
 #pragma unroll
-                for (int a = 0; a < L; ++a) {
-                    if constexpr (CW == 16) {
-                        ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(a * NB), v[a]);
-                    } else {
-                        ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)(a * NB), v[a]);
+                for (int b0 = 0; b0 < G::NBP; b0 += LB) {
+                    uint32_t v[LB][kNb];
+                    uint32_t v0[kNb];
+                    if (b0 == 0) ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(I0 * kNb), v0);
+#pragma unroll
+                    for (int j = 0; j < LB; ++j)
+                        if (b0 + j < G::NBP && b0 + j != I0)
+                            ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((b0 + j) * kNb), v[j]);
+                    ptx::tmem_wait_ld();
+                    if (b0 + LB >= G::NBP) {   // last batch: the accumulator set is free
+                        ptx::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(&acce[st]);
+                    }
+                    if (b0 == 0) {
+#pragma unroll
+                        for (int c = 0; c < kNb; ++c) acc[c] = __uint_as_float(v0[c]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < LB; ++j) {
+                        if (b0 + j < G::NBP && b0 + j != I0) {
+                            const int src = (lane + DLO + b0 + j) & 31;   // lane m + d of this block
+                            float tv[kNb];   // a block's shuffles in flight before the adds
+#pragma unroll
+                            for (int c = 0; c < kNb; ++c)
+                                tv[c] = __shfl_sync(0xffffffffu, __uint_as_float(v[j][c]), src);
+#pragma unroll
+                            for (int c = 0; c < kNb; ++c) acc[c] += tv[c];
+                        }
                     }
                 }
-                ptx::tmem_wait_ld();
-                ptx::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&acce[st]);   // accumulators are in registers: the set is free
-                float acc[CW];
-#pragma unroll
-                for (int c = 0; c < CW; ++c) acc[c] = __uint_as_float(v[R][c]);
-#pragma unroll
-                for (int a = 0; a < L; ++a) {
-                    if (a == R) continue;
-                    const int src = (lane + a - R) & 31;  // row this line's partial comes from
-#pragma unroll
-                    for (int c = 0; c < CW; ++c) acc[c] += __shfl_sync(0xffffffffu, __uint_as_float(v[a][c]), src);
-                }
-                // Stage this warp's outputs (its CW columns of the quarter's
-                // 32 - 2R rows) row-major in its own buffer with the TMA
-                // swizzle (16-byte chunk index XOR row bits; conflict-free
-                // 16-byte stores), then write them with one TMA store.
-                unsigned char* ost = outs + ((warp - 2 - kRoleWarps) * 2 + st) * OWB;
+                // Stage this warp's output rows (one parity of the quarter) with
+                // the TMA 64-byte swizzle (16-byte chunk XOR row bits), then
+                // one TMA store through the parity view.
+                unsigned char* ost = obuf + st * OWB;
                 if (lane == 0) ptx::bulk_wait_group_read<1>();   // this buffer's store of two tiles ago
                 __syncwarp();
-                if (lane >= R && lane < kSlabRows - R) {
-                    const int orow = lane - R;
+                if (lane >= G::DM && lane < kLanes - G::DM) {
+                    const int o = lane - G::DM;
 #pragma unroll
-                    for (int c = 0; c < CW; c += 4) {
-                        const int chunk = c >> 2;
-                        const int sw = (CW == 16) ? (chunk ^ ((orow >> 1) & 3)) : (chunk ^ ((orow >> 2) & 1));
-                        *reinterpret_cast<float4*>(ost + orow * (CW * 4) + sw * 16) =
+                    for (int c = 0; c < kNb; c += 4) {
+                        const int sw = (c >> 2) ^ ((o >> 1) & 3);
+                        *reinterpret_cast<float4*>(ost + o * (kNb * 4) + sw * 16) =
                             make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
                     }
                 }
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
-                const int ox = X0 + CW * sub, oy = Y0 + q * ROWS_OUT;
-                if (lane == 0 && ox < args.nx && oy < args.ny) {
-                    ptx::tma_store_2d(&tmap_out, ox, oy, ost);
+                const int oy = (Y0 + q * G::ROWS_OUT) / 2;   // first output row of the quarter, parity view
+                if (lane == 0 && X0 < args.nx && oy < prows) {
+                    ptx::tma_store_2d(omap, X0, oy, ost);
                     ptx::bulk_commit_group();
                 }
             }
-        }
+        };
+        if (p == 0)
+            drain(std::integral_constant<int, 0>{});
+        else
+            drain(std::integral_constant<int, 1>{});
     }
 
     // ---- teardown (also after an abort: every role has left its loop)
-    if (warp >= 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
+    if (warp >= 2 + kSplitWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
     if (*abort_flag) {
         // Let copies and MMAs still in flight land before the CTA gives up its
         // shared and tensor memory (each wait bounded again).
@@ -390,59 +416,66 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     }
 }
 
-template <int R, bool BF>
-constexpr auto kernel_for() {
-    return mx2d_kernel<R, tile_nb<BF>(2 * R + 1), BF>;
-}
-
 // ------------------------------------------------------------------ host side
-// Row-major 2D view of the grid; one box is a 32-row slab of an input tile
-// (pitch columns: the K window, widened to an odd number of 16-byte chunks).
-bool encode_tile_map_2d(CUtensorMap* map, const float* base, int ny, int nx, int pitch) {
-    auto enc = get_encode();
-    if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
-    cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
-    cuuint32_t box[2] = {(cuuint32_t)pitch, (cuuint32_t)kSlabRows};
-    cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+using MxKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, MxArgs2D);
+
+struct KernelInfo {
+    MxKernel fn = nullptr;
+    int smem = 0;
+};
+
+template <int R, bool BF>
+KernelInfo kernel_info() {
+    return {mx2d_kernel<R, BF>, smem_bytes<R, BF>()};
 }
 
-// Row-major 2D view of the output grid; one box is one epilogue warp's share
-// of a tile (NB/2 columns x (32-2r) rows), written from shared memory with the
-// TMA 64-byte (16 columns) or 32-byte (8 columns) swizzle.
-bool encode_out_map_2d(CUtensorMap* map, float* base, int ny, int nx, int cols, int rows) {
-    auto enc = get_encode();
-    if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
-    cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
-    cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
-    cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-using MxKernel = void (*)(CUtensorMap, CUtensorMap, MxArgs2D);
-
-MxKernel kernel_for_radius(int r, bool bf) {
+KernelInfo kernel_for(int r, bool bf) {
     switch (r) {
-        case 1: return bf ? kernel_for<1, true>() : kernel_for<1, false>();
-        case 2: return bf ? kernel_for<2, true>() : kernel_for<2, false>();
-        case 3: return bf ? kernel_for<3, true>() : kernel_for<3, false>();
-        case 4: return bf ? kernel_for<4, true>() : kernel_for<4, false>();
+        case 1: return bf ? kernel_info<1, true>() : kernel_info<1, false>();
+        case 2: return bf ? kernel_info<2, true>() : kernel_info<2, false>();
+        case 3: return bf ? kernel_info<3, true>() : kernel_info<3, false>();
+        case 4: return bf ? kernel_info<4, true>() : kernel_info<4, false>();
     }
-    return nullptr;
+    return {};
+}
+
+// Block list of order r: block (p, i) (lane offset d = dlo(p) + i) stacks
+// line 2d - p + r over line 2d - p + r + 1 (null outside 0..2r).
+std::vector<std::array<const double*, 2>> pair_blocks(int r, const double* cg) {
+    const int W = 2 * r + 1;
+    std::vector<std::array<const double*, 2>> out;
+    for (int p = 0; p < 2; ++p) {
+        const int dlo = -((r + 1 - p) / 2);
+        for (int i = 0; i <= r; ++i) {
+            std::array<const double*, 2> b{nullptr, nullptr};
+            for (int e = 0; e < 2; ++e) {
+                const int a = 2 * (dlo + i) - p + r + e;
+                if (a >= 0 && a <= 2 * r) b[e] = cg + a * W;
+            }
+            out.push_back(b);
+        }
+    }
+    return out;
+}
+
+// Row-parity view of a row-major grid: rows parity, parity + 2, ... (a 2D
+// tensor of rows_p rows with a row stride of two grid rows).
+bool encode_parity_map(CUtensorMap* map, const float* base, int rows_p, int nx, int box_x, int box_y,
+                       CUtensorMapSwizzle swz, CUtensorMapL2promotion l2) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows_p};
+    cuuint64_t strides[1] = {(cuuint64_t)nx * 8};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, l2, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 struct MxState {
     unsigned int* err_host = nullptr;  // host-mapped error word
     unsigned int* err_dev = nullptr;
     int num_sms = 0;
-    int nb = 32;          // output columns per tile
-    int in_w = 40;        // input columns per tile (the K window)
     bool bf = false;      // BF16 operands (else TF32)
     uint32_t bop_bytes = 0;
     uint32_t bpart_bytes = 0;
@@ -464,6 +497,10 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "the contiguous extent must be a multiple of 4 (16-byte TMA rows)";
         return false;
     }
+    if (q.n[0] < 2) {
+        if (why) *why = "the matrixized 2D kernel needs at least two rows";
+        return false;
+    }
     if (q.tb > 1) {
         if (why) *why = "temporal blocking not built for the matrixized kernel";
         return false;
@@ -480,19 +517,20 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->prec = q.prec;
     p->tb = 1;
     if (q.ndim == 3) return mx3d_plan_build(q, p, why);
-    const int W = 2 * q.r + 1;
-    const int L = W;            // every row a of C^g is one line along the contiguous axis
     const bool bf = is_bf16(q.prec);
-    const int NB = bf ? tile_nb<true>(L) : tile_nb<false>(L);
-    const int KW = bf ? OpFmt<true>::window(NB) : OpFmt<false>::window(NB);
-    p->nb = NB;
-    std::vector<const double*> lines;
-    for (int a = 0; a < L; ++a) lines.push_back(q.cg + a * W);
+    const int W = bf ? window<true>(kNb) : window<false>(kNb);
+    p->nb = kNb;
+    const auto blocks = pair_blocks(q.r, q.cg);
     uint32_t bpart = 0;
-    std::vector<unsigned char> ops = pack_bands(q.r, lines, NB, KW, bf, &bpart);
-    p->n_lines = L;
+    std::vector<unsigned char> ops = pack_blocks(q.r, blocks, kNb, W, bf, &bpart);
+    p->n_lines = 2 * q.r + 1;
     p->n_scalar = 0;
     p->operand_bytes = ops.size();
+    const KernelInfo ki = kernel_for(q.r, bf);
+    if (!ki.fn || ops.size() != (size_t)(bf ? 3 : 2) * bpart) {
+        if (why) *why = "internal error: block operand size";
+        return STENCIL_EUNSUPPORTED;
+    }
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {
         if (why) *why = std::string("operand upload: ") + cudaGetErrorString(e);
@@ -508,8 +546,6 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     MxState* st = new MxState();
     st->bop_bytes = (uint32_t)p->operand_bytes;
     st->bpart_bytes = bpart;
-    st->nb = NB;
-    st->in_w = KW;
     st->bf = bf;
     e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
@@ -525,21 +561,10 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     int dev = 0;
     cudaGetDevice(&dev);
     e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem);
     if (e != cudaSuccess) {
         mx_plan_free(p);
-        if (why) *why = std::string("device query: ") + cudaGetErrorString(e);
-        return STENCIL_ECUDA;
-    }
-    if (st->bop_bytes != (uint32_t)bop_bytes_2d(NB, L, bf)) {
-        mx_plan_free(p);
-        if (why) *why = "internal error: banded operand size";
-        return STENCIL_EUNSUPPORTED;
-    }
-    const size_t smem = smem_bytes_2d(NB, L, bf);
-    e = cudaFuncSetAttribute(kernel_for_radius(q.r, bf), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-        mx_plan_free(p);
-        if (why) *why = std::string("shared memory: ") + cudaGetErrorString(e);
+        if (why) *why = std::string("kernel set-up: ") + cudaGetErrorString(e);
         return STENCIL_ECUDA;
     }
     return STENCIL_OK;
@@ -572,9 +597,11 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     if (((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return cudaErrorMisalignedAddress;
     const MxState* st = (const MxState*)p.tmap_storage;
     const int ny = (int)p.n[0], nx = (int)p.n[1];
+    const int dm = (p.r + 1) / 2;
+    const int rows_out = 2 * (kLanes - 2 * dm);          // output rows per quarter
+    const int W = st->bf ? window<true>(kNb) : window<false>(kNb);
     MxArgs2D a;
     memset(&a, 0, sizeof(a));
-    a.out = (float*)dst;
     a.in = (const float*)src;
     a.bops = p.d_operands;
     a.err = st->err_dev;
@@ -584,19 +611,27 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.nparts = operand_parts(p.prec);
     a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;
-    const int in_w = st->in_w;
-    a.tiles_x = (nx + st->nb - 1) / st->nb;
-    const int tile_rows = kQuarters * (kSlabRows - 2 * p.r);   // output rows per tile
-    a.tiles_total = a.tiles_x * ((ny + tile_rows - 1) / tile_rows);
+    a.tiles_x = (nx + kNb - 1) / kNb;
+    a.tiles_total = a.tiles_x * ((ny + kQuarters * rows_out - 1) / (kQuarters * rows_out));
+    a.rows_even = (ny + 1) / 2;
+    a.rows_odd = ny / 2;
     a.bop_bytes = st->bop_bytes;
-    alignas(64) CUtensorMap map;
-    alignas(64) CUtensorMap map_out;
-    if (!encode_tile_map_2d(&map, (const float*)src, ny, nx, raw_pitch(in_w))) return cudaErrorInvalidValue;
-    if (!encode_out_map_2d(&map_out, (float*)dst, ny, nx, st->nb / kSubs, kSlabRows - 2 * p.r))
+    const float* in = (const float*)src;
+    float* out = (float*)dst;
+    alignas(64) CUtensorMap te, to, oe, oo;
+    const int kp = raw_pitch(W);
+    if (!encode_parity_map(&te, in, a.rows_even, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode_parity_map(&to, in + nx, a.rows_odd, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode_parity_map(&oe, out, a.rows_even, nx, kNb, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE) ||
+        !encode_parity_map(&oo, out + nx, a.rows_odd, nx, kNb, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE))
         return cudaErrorInvalidValue;
+    const KernelInfo ki = kernel_for(p.r, st->bf);
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    const int L = 2 * p.r + 1;
-    kernel_for_radius(p.r, st->bf)<<<grid, kThreads, smem_bytes_2d(st->nb, L, st->bf), s>>>(map, map_out, a);
+    ki.fn<<<grid, kThreads, ki.smem, s>>>(te, to, oe, oo, a);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <array>
 #include <vector>
 
 #include "plan.h"
@@ -201,6 +202,46 @@ inline float tf32_round(float x) {
 // H_l[k][q] = w_l[k - q - (4 - r)] (zero outside the band and for k >= nb + 8),
 // split into TF32 hi/lo parts or three BF16 parts.  Returns the bytes of one
 // part in *part_bytes.
+// Banded operand of a block list: block j stacks, along K, the band of line
+// blocks[j][0] (K rows 0 .. kh-1) over the band of line blocks[j][1] (rows
+// kh .. 2kh-1); a null line contributes zeros.  Used when one TMEM lane holds
+// two input rows side by side along K.
+inline std::vector<unsigned char> pack_blocks(int r, const std::vector<std::array<const double*, 2>>& blocks, int nb,
+                                              int kh, bool bf, uint32_t* part_bytes) {
+    const int nblk = (int)blocks.size(), N = nblk * nb, kw = 2 * kh;
+    const int epc = bf ? 8 : 4;  // elements per 16-byte chunk
+    const int es = bf ? 2 : 4;
+    const int parts = bf ? 3 : 2;
+    const size_t pb = (size_t)(kw / epc) * N * 16;
+    std::vector<unsigned char> out(parts * pb, 0);
+    std::vector<double> band((size_t)(nb + 8) * nb);
+    for (int j = 0; j < nblk; ++j)
+        for (int e = 0; e < 2; ++e) {
+            if (!blocks[j][e]) continue;
+            band_operand(r, blocks[j][e], nb, 4, band.data());
+            for (int kk = 0; kk < nb + 8; ++kk)
+                for (int q = 0; q < nb; ++q) {
+                    const int k = e * kh + kk;
+                    float rem = (float)band[(size_t)kk * nb + q];
+                    const size_t off = ((size_t)(k / epc) * N + (size_t)(j * nb + q)) * 16 + (size_t)(k % epc) * es;
+                    for (int p = 0; p < parts; ++p) {
+                        const float v = bf ? bf16_round(rem) : tf32_round(rem);
+                        rem -= v;
+                        if (bf) {
+                            uint32_t u;
+                            memcpy(&u, &v, 4);
+                            const uint16_t h = (uint16_t)(u >> 16);
+                            memcpy(&out[p * pb + off], &h, 2);
+                        } else {
+                            memcpy(&out[p * pb + off], &v, 4);
+                        }
+                    }
+                }
+        }
+    *part_bytes = (uint32_t)pb;
+    return out;
+}
+
 inline std::vector<unsigned char> pack_bands(int r, const std::vector<const double*>& lines, int nb, int kwin, bool bf,
                                              uint32_t* part_bytes) {
     const int L = (int)lines.size(), N = L * nb;
