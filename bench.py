@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
-                    choices=["box25-8192", "star7-512", "box27-512", "jacobi-256", "batch-1024", "serve-2000"])
+                    choices=["box25-8192", "star7-512", "box27-512", "sine7-512", "sine27-512", "jacobi-256",
+                             "batch-1024", "serve-2000"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
@@ -70,16 +71,24 @@ def workload(args):
         return si.cube_512(si.STAR, args.dtype or "f32", args.tsteps or 50, args.side or 512)
     if w == "box27-512":
         return si.cube_512(si.BOX, args.dtype or "f32", args.tsteps or 50, args.side or 512)
+    if w == "sine7-512":
+        return si.sine_cube_512(si.STAR, args.tsteps or 1000, args.side or 512)
+    if w == "sine27-512":
+        return si.sine_cube_512(si.BOX, args.tsteps or 1000, args.side or 512)
     p = si.jacobi_256(args.tsteps or 10)
     return p
 
 
 def workload_config(p, args, extra=None):
     desc = {"box25-8192": "2D box r=2 (25-point)", "star7-512": "3D 7-point star", "box27-512": "3D 27-point box",
+            "sine7-512": "3D 7-point star (centre 0.4, neighbours 0.1)",
+            "sine27-512": "3D 27-point separable box ((1/4,1/2,1/4)^3)",
             "jacobi-256": "2D 5-point Jacobi star"}[args.workload]
     grid_bytes = p.points * (4 if p.dtype == "f32" else 8)
+    fdesc = ("lowest sine mode field (exact result known in closed form)" if p.field_kind == "sine"
+             else "seeded synthetic field and coefficients")
     cfg = {"workload": f"{desc} {'x'.join(str(s) for s in p.shape)} {p.dtype.upper()}, {p.bc}, "
-                       f"{p.steps} time steps per solve, seeded synthetic field and coefficients",
+                       f"{p.steps} time steps per solve, {fdesc}",
            "grid": list(p.shape), "radius": p.r, "kind": p.kind, "boundary": p.bc,
            "time_steps_per_solve": p.steps,
            "l2_policy": (f"inputs larger than L2 (grid {grid_bytes / 2**20:.0f} MiB > 129 MB L2); no flush"
@@ -203,6 +212,18 @@ def sample_points(shape, n=8, seed=77):
     pts[0] = 0
     pts[1] = np.array(shape) - 1
     return pts
+
+
+def sine_closed_form(p, field, pts):
+    """lam^T times the initial sine mode at the sampled points, with
+    lam = sum_o C^g[o] prod_k cos(pi (o_k - r) / (n_k + 1)) (exact for C^g
+    symmetric in every axis and zero Dirichlet boundaries)."""
+    phi = [np.pi / (n + 1) for n in p.shape]
+    w = 2 * p.r + 1
+    lam = 0.0
+    for o in np.ndindex(*([w] * p.ndim)):
+        lam += p.coeffs[o] * np.prod([np.cos(ph * (ok - p.r)) for ph, ok in zip(phi, o)])
+    return lam ** p.steps * field[tuple(pts.T)]
 
 
 # ------------------------------------------------------------------ reference arm
@@ -449,7 +470,12 @@ def main():
     # accuracy of each implementation at sampled points (oracle on the dependency cone)
     import oracle
     pts = sample_points(p.shape)
-    want = oracle.sample(field, p.r, p.coeffs, p.bc, p.steps, pts) if rank == 0 else None
+    if p.field_kind == "sine":
+        # long runs: every point depends on the whole grid, so the check is
+        # the closed form (the field is an eigenvector of the symmetric stencil)
+        want = sine_closed_form(p, field, pts)
+    else:
+        want = oracle.sample(field, p.r, p.coeffs, p.bc, p.steps, pts) if rank == 0 else None
     for impl, res in results.items():
         if "plan" not in res:
             continue

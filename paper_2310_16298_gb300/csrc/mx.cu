@@ -40,8 +40,8 @@
 //  * warps 10..17: epilogue warps, one per (quarter, output parity): tensor
 //    memory -> shuffles -> swizzled smem -> TMA store through the output
 //    row-parity tensor map.
-// Two or three A stages (as many as tensor memory holds beside two
-// accumulator sets) overlap split, MMA and epilogue; every wait is bounded
+// Two or three accumulator sets and A stages (as many as tensor memory
+// holds) overlap split, MMA and epilogue; every wait is bounded
 // (a timeout sets a host-visible error word, drains copies in flight and
 // frees tensor memory).
 //
@@ -72,7 +72,9 @@ using namespace mxu;
 constexpr int kPad = 4;                 // input columns left of the output block
 constexpr int kLanes = 32;              // TMEM lanes per warp (lane quarter)
 constexpr int kQuarters = 4;
-constexpr int kNb = 16;                 // output columns per tile
+constexpr int kNb = 16;                 // output columns per MMA item
+constexpr int kItems = 2;               // items (16-column blocks) per tile
+constexpr int kTw = kItems * kNb;       // output columns per tile
 constexpr int kSplitWarps = 2 * kQuarters;   // (quarter, input row parity)
 constexpr int kEpiWarps = 2 * kQuarters;     // (quarter, output row parity)
 constexpr int kThreads = 64 + 32 * (kSplitWarps + kEpiWarps);
@@ -100,12 +102,16 @@ __host__ __device__ constexpr int window(int nb) { return BF ? OpFmt<true>::wind
 // Shared-memory row pitch of the raw tile: the window widened to an odd
 // number of 16-byte chunks (eight consecutive rows = eight bank groups).
 __host__ __device__ constexpr int raw_pitch(int w) { return ((w / 4) & 1) ? w : w + 4; }
+// Raw tile row: the windows of all items of a tile (item j starts 16 j columns in).
 template <bool BF>
-__host__ __device__ constexpr int raw_stage_bytes() { return 2 * kQuarters * kLanes * raw_pitch(window<BF>(kNb)) * 4; }
+__host__ __device__ constexpr int raw_row(int nb) { return nb * (kItems - 1) + window<BF>(nb); }
+template <bool BF>
+__host__ __device__ constexpr int raw_stage_bytes() { return 2 * kQuarters * kLanes * raw_pitch(raw_row<BF>(kNb)) * 4; }
 
-// Output staging: two buffers per epilogue warp of (32 - 2 DM) rows x 16 floats.
-__host__ __device__ constexpr int out_warp_bytes() { return 2048; }
-__host__ __device__ constexpr int out_bytes() { return kEpiWarps * 2 * out_warp_bytes(); }
+// Output staging: one buffer per epilogue warp of (32 - 2 DM) rows x kTw floats
+// (both items of a tile, written with one TMA store).
+__host__ __device__ constexpr int out_warp_bytes() { return 32 * kTw * 4; }
+__host__ __device__ constexpr int out_bytes() { return kEpiWarps * out_warp_bytes(); }
 
 template <int R, bool BF>
 __host__ __device__ constexpr int bop_bytes() {
@@ -137,7 +143,19 @@ struct MxArgs2D {
     int nprod;                 // products per K step (1, 3 or 6)
 };
 
-template <int R, bool BF>
+// Tensor-memory stage counts for A operands of a_cols columns and
+// accumulator sets of n columns: as many A stages as fit (up to 4) beside two
+// accumulator sets, then as many accumulator sets as fit beside those.
+__host__ __device__ constexpr int a_stages(int a_cols, int n) {
+    return (4 * a_cols + 2 * n <= kTmemCols) ? 4 : (3 * a_cols + 2 * n <= kTmemCols) ? 3 : 2;
+}
+__host__ __device__ constexpr int d_sets(int a_cols, int n) {
+    return (a_stages(a_cols, n) * a_cols + 4 * n <= kTmemCols)   ? 4
+           : (a_stages(a_cols, n) * a_cols + 3 * n <= kTmemCols) ? 3
+                                                                 : 2;
+}
+
+template <int R, bool BF, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
 mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ CUtensorMap tmap_o,
             const __grid_constant__ CUtensorMap omap_e, const __grid_constant__ CUtensorMap omap_o,
@@ -149,25 +167,29 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     constexpr int KW = 2 * W;               // K: even-row window | odd-row window
     constexpr int KS = KW / F::kKStep;      // MMAs per product
     constexpr int PC = F::part_cols(KW);    // TMEM columns of one operand part
-    constexpr int A_COLS = F::kMaxParts * PC;
+    constexpr int A_COLS = NP * PC;         // NP operand parts (1..3) per A stage
     constexpr int GW = F::kGroup;           // input columns per split group
     constexpr int NG = W / GW;              // split groups per row
     constexpr int WU = kNb + 2 * kPad;      // window columns that carry weights
-    constexpr int KP = raw_pitch(W);
+    constexpr int KP = raw_pitch(raw_row<BF>(kNb));
     constexpr int SLAB = kLanes * KP * 4;   // one (parity, quarter) box
     constexpr int RSB = raw_stage_bytes<BF>();
     constexpr int kRawStages = raw_stages<R, BF>();
     constexpr int OWB = out_warp_bytes();
-    constexpr int AST = (3 * A_COLS + 2 * N <= kTmemCols) ? 3 : 2;   // A operand stages in TMEM
-    static_assert(kRawStages >= 3, "TMA ring too shallow");
+    // A stages hide the split -> MMA -> completion -> split round trip,
+    // accumulator sets the MMA -> epilogue -> MMA one
+    constexpr int AST = a_stages(A_COLS, N);
+    constexpr int DST = d_sets(A_COLS, N);
+    static_assert(kRawStages * kItems >= 4, "TMA ring too shallow");
     static_assert(N % 16 == 0 && N <= 256, "MMA N");
     static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
-    static_assert(2 * kRawStages + 2 * AST + 5 <= 2 * kMaxRawStages + 15, "barrier space");
-    static_assert(G::LANES_OUT * kNb * 4 <= OWB, "output staging");
+    static_assert(AST * A_COLS + DST * N <= kTmemCols, "TMEM budget");
+    static_assert(2 * kRawStages + 2 * AST + 2 * DST + 1 <= 2 * kMaxRawStages + 15, "barrier space");
+    static_assert(G::LANES_OUT * kTw * 4 <= OWB && kTw * 4 == 128, "output staging (128-byte swizzle rows)");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* outs = smem;                     // [epilogue warp][2] output buffers (1 KB aligned)
+    unsigned char* outs = smem;                     // [epilogue warp] output buffers (1 KB aligned)
     unsigned char* raw = outs + out_bytes();        // [stage][parity][quarter] 32-row boxes
     unsigned char* bops = raw + kRawStages * RSB;
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
@@ -175,9 +197,9 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     uint64_t* rawfree = bars + kRawStages;          // [kRawStages] rows read by the split warps
     uint64_t* afull = bars + 2 * kRawStages;        // [AST] A operand stage written to TMEM
     uint64_t* aempty = afull + AST;                 // [AST] MMAs done reading the A stage
-    uint64_t* accf = aempty + AST;                  // [2] accumulator set ready
-    uint64_t* acce = accf + 2;                      // [2] accumulator set drained
-    uint64_t* bop_bar = acce + 2;
+    uint64_t* accf = aempty + AST;                  // [DST] accumulator set ready
+    uint64_t* acce = accf + DST;                    // [DST] accumulator set drained
+    uint64_t* bop_bar = acce + DST;
     uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -193,7 +215,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             ptx::mbar_init(&afull[a], kSplitWarps);
             ptx::mbar_init(&aempty[a], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < DST; ++a) {
             ptx::mbar_init(&accf[a], 1);
             ptx::mbar_init(&acce[a], kEpiWarps);
         }
@@ -210,7 +232,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tmem_a = tmem;                             // A stages: [AST][parts]
-    const uint32_t tmem_d = tmem + (uint32_t)(AST * A_COLS);  // accumulator sets: [2][N]
+    const uint32_t tmem_d = tmem + (uint32_t)(AST * A_COLS);  // accumulator sets: [DST][N]
     int issued = 0;        // producer: TMA tiles issued
     int committed = -1;    // MMA issuer: last tile whose MMAs were committed
 
@@ -224,7 +246,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
                 if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag)) break;
-                const int X0 = (t % args.tiles_x) * kNb;
+                const int X0 = (t % args.tiles_x) * kTw;
                 const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
                 unsigned char* dst = raw + s * RSB;
                 ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)RSB);
@@ -245,13 +267,17 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
             const int pr = args.nprod;
             int i = 0;
-            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x)
+            for (int j = 0; j < kItems; ++j, ++i) {
                 const int sa = i % AST;
                 const uint32_t pa = (uint32_t)(i / AST) & 1u;
-                const int st = i & 1;
-                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                if (!wait_or_abort(&afull[sa], pa, abort_flag)) break;
-                if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
+                const int st = i % DST;
+                const uint32_t ph = (uint32_t)(i / DST) & 1u;
+                if (!wait_or_abort(&afull[sa], pa, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 ptx::tc_fence_after();
                 issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
                                        args.bpart_bytes, N, idesc, pr);
@@ -265,56 +291,65 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
         const int q = warp & 3;                        // TMEM lane quarter of this warp
         const int e = (warp - 2) >> 2;                 // input row parity this warp converts
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        int i = 0;
-        for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
-            const int rs = i % kRawStages;
-            const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
-            const int sa = i % AST;
-            const uint32_t pa = (uint32_t)(i / AST) & 1u;
+        int i = 0, k = 0;   // items, tiles
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x, ++k) {
+            const int rs = k % kRawStages;
+            const uint32_t rph = (uint32_t)(k / kRawStages) & 1u;
             if (!wait_or_abort(&full[rs], rph, abort_flag)) break;
-            const int X0 = (t % args.tiles_x) * kNb;
+            const int X0 = (t % args.tiles_x) * kTw;
             const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
             const int gy = Y0 + q * G::ROWS_OUT - 2 * G::DM + 2 * lane + e;   // input row of this thread
-            const bool fix = (args.bc == kBcPeriodic) &&
-                             (gy < 0 || gy >= args.ny || X0 - kPad < 0 || X0 - kPad + WU > args.nx);
             const float* row =
                 reinterpret_cast<const float*>(raw + rs * RSB + (e * kQuarters + q) * SLAB) + (size_t)lane * KP;
-            float x[NG][GW];
+            for (int j = 0; j < kItems; ++j, ++i) {
+                const int sa = i % AST;
+                const uint32_t pa = (uint32_t)(i / AST) & 1u;
+                const int xj = X0 + kNb * j;             // first output column of the item
+                const bool fix = (args.bc == kBcPeriodic) &&
+                                 (gy < 0 || gy >= args.ny || xj - kPad < 0 || xj - kPad + WU > args.nx);
+                float x[NG][GW];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
+                for (int g = 0; g < NG; ++g) {
 #pragma unroll
-                for (int c4 = 0; c4 < GW; c4 += 4) {
-                    float4 v = *reinterpret_cast<const float4*>(row + GW * g + c4);
-                    if (fix) {
-                        const int gx = X0 - kPad + GW * g + c4;
-                        if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
-                            v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
-                                                                 wrap_index(gx, args.nx));
+                    for (int c4 = 0; c4 < GW; c4 += 4) {
+                        float4 v = *reinterpret_cast<const float4*>(row + kNb * j + GW * g + c4);
+                        if (fix) {
+                            const int gx = xj - kPad + GW * g + c4;
+                            if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
+                                v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
+                                                                     wrap_index(gx, args.nx));
+                        }
+                        x[g][c4] = v.x;
+                        x[g][c4 + 1] = v.y;
+                        x[g][c4 + 2] = v.z;
+                        x[g][c4 + 3] = v.w;
                     }
-                    x[g][c4] = v.x;
-                    x[g][c4 + 1] = v.y;
-                    x[g][c4 + 2] = v.z;
-                    x[g][c4 + 3] = v.w;
                 }
-            }
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&rawfree[rs]);   // the rows are in registers
-            if (!wait_or_abort(&aempty[sa], pa ^ 1u, abort_flag)) break;
-            ptx::tc_fence_after();
-            const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
+                if (j == kItems - 1) {   // every item's rows are in registers: the stage goes back
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&rawfree[rs]);
+                }
+                if (!wait_or_abort(&aempty[sa], pa ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
 #pragma unroll
-            for (int g = 0; g < NG; ++g) split_store<BF>(x[g], abase, PC, e * W + GW * g, args.nparts);
-            ptx::tmem_wait_st();
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&afull[sa]);
+                for (int g = 0; g < NG; ++g) split_store<BF, NP>(x[g], abase, PC, e * W + GW * g);
+                ptx::tmem_wait_st();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&afull[sa]);
+            }
         }
     } else {
         // ------------------------------------------------ epilogue: accumulators -> outputs
         const int q = warp & 3;
         const int p = (warp - 2 - kSplitWarps) >> 2;   // output row parity of this warp
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        unsigned char* obuf = outs + (warp - 2 - kSplitWarps) * 2 * OWB;
+        unsigned char* ost = outs + (warp - 2 - kSplitWarps) * OWB;
         auto drain = [&](auto pc) {
             constexpr int P = decltype(pc)::value;
             constexpr int DLO = G::dlo(P);
@@ -323,12 +358,17 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             const CUtensorMap* omap = P ? &omap_o : &omap_e;
             const int prows = P ? args.rows_odd : args.rows_even;
             int i = 0;
-            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
-                const int st = i & 1;
-                const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                if (!wait_or_abort(&accf[st], ph, abort_flag)) break;
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x)
+            for (int j = 0; j < kItems; ++j, ++i) {
+                const int st = i % DST;
+                const uint32_t ph = (uint32_t)(i / DST) & 1u;
+                if (!wait_or_abort(&accf[st], ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 ptx::tc_fence_after();
-                const int X0 = (t % args.tiles_x) * kNb;
+                const int X0 = (t % args.tiles_x) * kTw;
                 const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
                 const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + P * G::NBP * kNb);
                 float acc[kNb];
@@ -364,27 +404,31 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                         }
                     }
                 }
-                // Stage this warp's output rows (one parity of the quarter) with
-                // the TMA 64-byte swizzle (16-byte chunk XOR row bits), then
-                // one TMA store through the parity view.
-                unsigned char* ost = obuf + st * OWB;
-                if (lane == 0) ptx::bulk_wait_group_read<1>();   // this buffer's store of two tiles ago
-                __syncwarp();
+                // Stage this warp's output rows (one parity of the quarter,
+                // item j's 16 columns of the tile's 32) with the TMA 128-byte
+                // swizzle (16-byte chunk XOR row bits), then one TMA store per
+                // tile through the parity view.
+                if (j == 0) {
+                    if (lane == 0) ptx::bulk_wait_group_read<0>();   // the previous tile's store has read the buffer
+                    __syncwarp();
+                }
                 if (lane >= G::DM && lane < kLanes - G::DM) {
                     const int o = lane - G::DM;
 #pragma unroll
                     for (int c = 0; c < kNb; c += 4) {
-                        const int sw = (c >> 2) ^ ((o >> 1) & 3);
-                        *reinterpret_cast<float4*>(ost + o * (kNb * 4) + sw * 16) =
+                        const int sw = ((kNb * j + c) >> 2) ^ (o & 7);
+                        *reinterpret_cast<float4*>(ost + o * (kTw * 4) + sw * 16) =
                             make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
                     }
                 }
-                ptx::fence_proxy_async_smem();
-                __syncwarp();
-                const int oy = (Y0 + q * G::ROWS_OUT) / 2;   // first output row of the quarter, parity view
-                if (lane == 0 && X0 < args.nx && oy < prows) {
-                    ptx::tma_store_2d(omap, X0, oy, ost);
-                    ptx::bulk_commit_group();
+                if (j == kItems - 1) {
+                    ptx::fence_proxy_async_smem();
+                    __syncwarp();
+                    const int oy = (Y0 + q * G::ROWS_OUT) / 2;   // first output row of the quarter, parity view
+                    if (lane == 0 && X0 < args.nx && oy < prows) {
+                        ptx::tma_store_2d(omap, X0, oy, ost);
+                        ptx::bulk_commit_group();
+                    }
                 }
             }
         };
@@ -404,7 +448,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 if (k >= 0) ptx::mbar_wait(&full[k % kRawStages], (uint32_t)(k / kRawStages) & 1u, kWaitCycles / 8);
         }
         if (warp == 1 && lane == 0 && committed >= 0)
-            ptx::mbar_wait(&accf[committed & 1], (uint32_t)(committed >> 1) & 1u, kWaitCycles / 8);
+            ptx::mbar_wait(&accf[committed % DST], (uint32_t)(committed / DST) & 1u, kWaitCycles / 8);
     }
     __syncwarp();
     if (tid == 0 && *abort_flag) atomicOr(args.err, 1u);
@@ -424,17 +468,24 @@ struct KernelInfo {
     int smem = 0;
 };
 
-template <int R, bool BF>
+template <int R, bool BF, int NP>
 KernelInfo kernel_info() {
-    return {mx2d_kernel<R, BF>, smem_bytes<R, BF>()};
+    return {mx2d_kernel<R, BF, NP>, smem_bytes<R, BF>()};
 }
 
-KernelInfo kernel_for(int r, bool bf) {
+template <int R>
+KernelInfo kernel_for_parts(bool bf, int np) {
+    if (bf) return np == 1 ? kernel_info<R, true, 1>() : np == 2 ? kernel_info<R, true, 2>() : kernel_info<R, true, 3>();
+    return np == 1 ? kernel_info<R, false, 1>() : kernel_info<R, false, 2>();
+}
+
+// Kernel of order r for BF16 (else TF32) operands split into np parts.
+KernelInfo kernel_for(int r, bool bf, int np) {
     switch (r) {
-        case 1: return bf ? kernel_info<1, true>() : kernel_info<1, false>();
-        case 2: return bf ? kernel_info<2, true>() : kernel_info<2, false>();
-        case 3: return bf ? kernel_info<3, true>() : kernel_info<3, false>();
-        case 4: return bf ? kernel_info<4, true>() : kernel_info<4, false>();
+        case 1: return kernel_for_parts<1>(bf, np);
+        case 2: return kernel_for_parts<2>(bf, np);
+        case 3: return kernel_for_parts<3>(bf, np);
+        case 4: return kernel_for_parts<4>(bf, np);
     }
     return {};
 }
@@ -526,7 +577,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->n_lines = 2 * q.r + 1;
     p->n_scalar = 0;
     p->operand_bytes = ops.size();
-    const KernelInfo ki = kernel_for(q.r, bf);
+    const KernelInfo ki = kernel_for(q.r, bf, operand_parts(q.prec));
     if (!ki.fn || ops.size() != (size_t)(bf ? 3 : 2) * bpart) {
         if (why) *why = "internal error: block operand size";
         return STENCIL_EUNSUPPORTED;
@@ -599,7 +650,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     const int ny = (int)p.n[0], nx = (int)p.n[1];
     const int dm = (p.r + 1) / 2;
     const int rows_out = 2 * (kLanes - 2 * dm);          // output rows per quarter
-    const int W = st->bf ? window<true>(kNb) : window<false>(kNb);
+    const int RWD = st->bf ? raw_row<true>(kNb) : raw_row<false>(kNb);
     MxArgs2D a;
     memset(&a, 0, sizeof(a));
     a.in = (const float*)src;
@@ -611,7 +662,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.nparts = operand_parts(p.prec);
     a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;
-    a.tiles_x = (nx + kNb - 1) / kNb;
+    a.tiles_x = (nx + kTw - 1) / kTw;
     a.tiles_total = a.tiles_x * ((ny + kQuarters * rows_out - 1) / (kQuarters * rows_out));
     a.rows_even = (ny + 1) / 2;
     a.rows_odd = ny / 2;
@@ -619,17 +670,17 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     const float* in = (const float*)src;
     float* out = (float*)dst;
     alignas(64) CUtensorMap te, to, oe, oo;
-    const int kp = raw_pitch(W);
+    const int kp = raw_pitch(RWD);
     if (!encode_parity_map(&te, in, a.rows_even, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
         !encode_parity_map(&to, in + nx, a.rows_odd, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
-        !encode_parity_map(&oe, out, a.rows_even, nx, kNb, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_64B,
+        !encode_parity_map(&oe, out, a.rows_even, nx, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE) ||
-        !encode_parity_map(&oo, out + nx, a.rows_odd, nx, kNb, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_64B,
+        !encode_parity_map(&oo, out + nx, a.rows_odd, nx, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE))
         return cudaErrorInvalidValue;
-    const KernelInfo ki = kernel_for(p.r, st->bf);
+    const KernelInfo ki = kernel_for(p.r, st->bf, operand_parts(p.prec));
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
     ki.fn<<<grid, kThreads, ki.smem, s>>>(te, to, oe, oo, a);
     return cudaGetLastError();

@@ -20,9 +20,12 @@ namespace mxu {
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // Bounded mbarrier wait that also gives up once another role has failed.
+// Between polls the warp sleeps briefly, so that waiting warps leave the
+// issue slots (and the shared-memory pipe) to the warps doing the work.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     const long long t0 = clock64();
     while (!ptx::mbar_try_wait(bar, parity)) {
+        __nanosleep(64);
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             *abort_flag = 1;
@@ -122,40 +125,48 @@ __device__ __forceinline__ void issue_products(uint32_t d, uint32_t a_base, int 
     issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 0, nprod == 1);
 }
 
-// Split kGroup input values into the operand parts and write them to the
+// Split kGroup input values into NP operand parts and write them to the
 // warp's tensor-memory lanes at column c (part p at a_base + p*part_cols).
-template <bool BF>
-__device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int part_cols, int c, int nparts) {
+template <bool BF, int NP>
+__device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int part_cols, int c) {
     if constexpr (!BF) {
         uint32_t h[8], l[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             h[e] = tf32_hi_bits(x[e]);
-            l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
+            if constexpr (NP > 1) l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
         }
         ptx::tmem_st_32x32b_x8(a_base + (uint32_t)c, h);
-        if (nparts > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c), l);
+        if constexpr (NP > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c), l);
     } else {
-        uint32_t w[3][8];
+        uint32_t w[NP][8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             float r0a = x[2 * e], r0b = x[2 * e + 1];
-            uint32_t pa[3], pb[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < NP; ++k) {
                 const uint32_t ba = bf16_rn_bits(r0a), bb = bf16_rn_bits(r0b);
-                pa[k] = ba;
-                pb[k] = bb;
-                r0a -= __uint_as_float(ba << 16);
-                r0b -= __uint_as_float(bb << 16);
+                w[k][e] = ba | (bb << 16);
+                if (k + 1 < NP) {
+                    r0a -= __uint_as_float(ba << 16);
+                    r0b -= __uint_as_float(bb << 16);
+                }
             }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) w[k][e] = pa[k] | (pb[k] << 16);
         }
-        ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(c / 2), w[0]);
-        if (nparts > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c / 2), w[1]);
-        if (nparts > 2) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(2 * part_cols + c / 2), w[2]);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(k * part_cols + c / 2), w[k]);
     }
+}
+
+// Run-time part count (kernels not specialised on it).
+template <bool BF>
+__device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int part_cols, int c, int nparts) {
+    if (nparts == 1)
+        split_store<BF, 1>(x, a_base, part_cols, c);
+    else if (nparts == 2 || !BF)
+        split_store<BF, 2>(x, a_base, part_cols, c);
+    else
+        split_store<BF, 3>(x, a_base, part_cols, c);
 }
 
 inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {

@@ -150,8 +150,11 @@ class Problem:
     field_lo: float = 0.0
     field_hi: float = 1.0
     name: str = ""
+    field_kind: str = "uniform"   # 'uniform' (seeded) | 'sine' (lowest Dirichlet mode)
 
     def field(self) -> np.ndarray:
+        if self.field_kind == "sine":
+            return round_to(sine_mode(self.shape), self.dtype)
         return round_to(field_uniform(self.shape, self.field_seed, self.field_lo, self.field_hi),
                         self.dtype)
 
@@ -162,6 +165,25 @@ class Problem:
     @property
     def updates(self) -> int:
         return self.points * self.steps
+
+
+def sine_mode(shape: Sequence[int]) -> np.ndarray:
+    """prod_k sin(pi (x_k + 1) / (n_k + 1)): the lowest mode of the zero-Dirichlet
+    grid of the given interior shape."""
+    f = np.ones(tuple(shape))
+    for k, n in enumerate(shape):
+        s = np.sin(np.pi * (np.arange(n, dtype=np.float64) + 1) / (n + 1))
+        f = f * s.reshape([n if j == k else 1 for j in range(len(shape))])
+    return f
+
+
+def sine_cube_512(kind: str, steps: int = 1000, side: int = 512) -> Problem:
+    """Long FP64 run: 512^3, 7-point star (centre 0.4, neighbours 0.1) or
+    27-point separable box ((1/4, 1/2, 1/4)^3), zero Dirichlet, started from
+    the lowest sine mode, so the exact result is a known multiple of it."""
+    cg = coeffs_symmetric_3d7p() if kind == STAR else coeffs_separable_3d27p()
+    return Problem(3, (side,) * 3, 1, kind, cg, "f64", DIRICHLET, steps, 0, field_kind="sine",
+                   name=f"3d{'7p' if kind == STAR else '27p'}-sine-{side}-f64")
 
 
 def jacobi_256(steps: int = 10) -> Problem:
