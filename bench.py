@@ -162,24 +162,34 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
+# Sources that build each kernel family (the ncu traffic of a kernel stays
+# valid while these files are unchanged).
+KERNEL_SOURCES = {
+    "matrixized-f32-2d": ("mx.cu", "mxutil.cuh", "ptx.cuh", "common.cuh", "mx.h", "plan.cpp", "plan.h"),
+    "matrixized-f32-3d": ("mx3d.cu", "mxutil.cuh", "ptx.cuh", "common.cuh", "mx.h", "plan.cpp", "plan.h"),
+    "gather": ("gather.cu", "common.cuh", "kernels.h"),
+}
+
+
+def kernel_source_hash(kernel_key):
+    fam = next((k for k in KERNEL_SOURCES if kernel_key.startswith(k)), None)
     csrc = os.path.join(ROOT, "paper_2310_16298_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES[fam] if fam else sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key):
     """Per-launch DRAM bytes for the kernel from the committed ncu summary,
-    valid only while the kernel sources are unchanged."""
+    valid only while the kernel's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel_key):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -128,7 +128,12 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
     static_assert(kRawStages >= 3, "TMA ring too shallow");
     static_assert(N <= 256 && N % 16 == 0, "MMA N");
-    static_assert(2 * A_COLS + 2 * N <= kTmemCols, "TMEM budget");
+    // A stages hide the split -> MMA -> completion -> split round trip,
+    // accumulator sets the MMA -> epilogue -> MMA one (as many as TMEM holds)
+    constexpr int AST = (4 * A_COLS + 2 * N <= kTmemCols) ? 4 : (3 * A_COLS + 2 * N <= kTmemCols) ? 3 : 2;
+    constexpr int DST = (AST * A_COLS + 3 * N <= kTmemCols) ? 3 : 2;
+    static_assert(AST * A_COLS + DST * N <= kTmemCols, "TMEM budget");
+    static_assert(2 * kRawStages + 2 * AST + 2 * DST + 1 <= 2 * kMaxRawStages + 15, "barrier space");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -138,11 +143,11 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     uint64_t* bars = (uint64_t*)(bops + args.bop_bytes);
     uint64_t* full = bars;
     uint64_t* rawfree = bars + kRawStages;
-    uint64_t* afull = bars + 2 * kRawStages;
-    uint64_t* aempty = afull + 2;
-    uint64_t* accf = aempty + 2;
-    uint64_t* acce = accf + 2;
-    uint64_t* bop_bar = acce + 2;
+    uint64_t* afull = bars + 2 * kRawStages;   // [AST]
+    uint64_t* aempty = afull + AST;            // [AST]
+    uint64_t* accf = aempty + AST;             // [DST]
+    uint64_t* acce = accf + DST;               // [DST]
+    uint64_t* bop_bar = acce + DST;
     uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -154,9 +159,11 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&rawfree[s], kRoleWarps);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < AST; ++a) {
             ptx::mbar_init(&afull[a], kRoleWarps);
             ptx::mbar_init(&aempty[a], 1);
+        }
+        for (int a = 0; a < DST; ++a) {
             ptx::mbar_init(&accf[a], 1);
             ptx::mbar_init(&acce[a], kRoleWarps);
         }
@@ -173,7 +180,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tmem_a = tmem;
-    const uint32_t tmem_d = tmem + (uint32_t)(2 * A_COLS);
+    const uint32_t tmem_d = tmem + (uint32_t)(AST * A_COLS);
     int issued = 0, committed = -1;
 
     // unit u -> (x tile, y tile, z chunk), x fastest
@@ -218,16 +225,18 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             bool ok = true;
             for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
                 for (int iz = 0; iz < PLANES; ++iz, ++i) {
-                    const int st = i & 1;
-                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                    if (!wait_or_abort(&afull[st], ph, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
+                    const int sa = i % AST;
+                    const uint32_t pa = (uint32_t)(i / AST) & 1u;
+                    const int st = i % DST;
+                    const uint32_t ph = (uint32_t)(i / DST) & 1u;
+                    if (!wait_or_abort(&afull[sa], pa, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(st * A_COLS), PC, b0,
+                    issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
                                            args.bpart_bytes, N, idesc, pr);
-                    ptx::mma_commit(&aempty[st]);
+                    ptx::mma_commit(&aempty[sa]);
                     ptx::mma_commit(&accf[st]);
                     committed = i;
                 }
@@ -245,15 +254,15 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 for (int iz = 0; iz < PLANES; ++iz, ++i) {
                     const int rs = i % kRawStages;
                     const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
-                    const int st = i & 1;
-                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-                    if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[st], ph ^ 1u, abort_flag)) {
+                    const int sa = i % AST;
+                    const uint32_t pa = (uint32_t)(i / AST) & 1u;
+                    if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[sa], pa ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
                     const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
-                    const uint32_t abase = tmem_a + lane_off + (uint32_t)(st * A_COLS);
+                    const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
 #pragma unroll
                     for (int g0 = 0; g0 < NG; g0 += kSubs) {
                         const int g = g0 + sub;
@@ -275,7 +284,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     __syncwarp();
                     if (lane == 0) {
                         ptx::mbar_arrive(&rawfree[rs]);
-                        ptx::mbar_arrive(&afull[st]);
+                        ptx::mbar_arrive(&afull[sa]);
                     }
                 }
             }
@@ -290,8 +299,8 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
 #pragma unroll
                     for (int c = 0; c < CW; ++c) acc[j][c] = 0.0f;
                 for (int iz = 0; iz < PLANES; ++iz, ++i) {
-                    const int st = i & 1;
-                    const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+                    const int st = i % DST;
+                    const uint32_t ph = (uint32_t)(i / DST) & 1u;
                     if (!wait_or_abort(&accf[st], ph, abort_flag)) {
                         ok = false;
                         break;
@@ -377,7 +386,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 if (k >= 0) ptx::mbar_wait(&full[k % kRawStages], (uint32_t)(k / kRawStages) & 1u, kWaitCycles / 8);
         }
         if (warp == 1 && lane == 0 && committed >= 0)
-            ptx::mbar_wait(&accf[committed & 1], (uint32_t)(committed >> 1) & 1u, kWaitCycles / 8);
+            ptx::mbar_wait(&accf[committed % DST], (uint32_t)(committed / DST) & 1u, kWaitCycles / 8);
     }
     __syncwarp();
     if (tid == 0 && *abort_flag) atomicOr(args.err, 1u);
