@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--dtype", default="", choices=["", "f32", "f64"], help="storage type ('' = the workload's own)")
     ap.add_argument("--prec", default="native", choices=["native", "tf32", "tf32x3", "bf16", "bf16x2", "bf16x3"],
                     help="matrixized arithmetic (native = TF32x3 for FP32)")
+    ap.add_argument("--cover", default="auto", choices=["auto", "parallel", "hybrid"],
+                    help="line cover of star stencils on the matrixized kernel")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -469,7 +471,8 @@ def main():
     for impl in ("matrixized", "gather"):
         try:
             plan = sx.Plan(p.shape, p.r, p.kind, p.coeffs, p.dtype, bc=p.bc, impl=impl,
-                           prec=args.prec if impl == "matrixized" else "native")
+                           prec=args.prec if impl == "matrixized" else "native",
+                           cover=args.cover if impl == "matrixized" else "auto")
         except sx.StencilError as e:
             results[impl] = {"unavailable": str(e)}
             continue
@@ -595,7 +598,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": p.dtype, "data": "synthetic",
-                "config": workload_config(p, args, {"impl": main_impl, "prec": info["prec"], "tb": tb,
+                "config": workload_config(p, args, {"impl": main_impl, "prec": info["prec"], "tb": tb, "cover": args.cover,
                                                     "parallelism": f"replicas x{world}"}),
                 "p50_ms": float(np.percentile(per_solve, 50)), "p99_ms": float(np.percentile(per_solve, 99)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

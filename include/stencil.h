@@ -81,12 +81,26 @@ typedef enum {
     STENCIL_IMPL_MATRIXIZED = 2  /* tensor-core outer-product kernel                    */
 } stencil_impl;
 
+/* Coefficient-line cover of a star stencil on the matrixized kernel (Sec. 4.1,
+ * Tables cls-2d / cls-3d).  PARALLEL: every line along the contiguous axis
+ * goes to the tensor cores (off-axis weights as one-diagonal bands).  HYBRID:
+ * only the contiguous-axis line (and an identity band that returns the input
+ * rows) goes to the tensor cores; the 2*ndim*r - 2r off-axis weights are
+ * applied on the CUDA cores to those rows in FP32.  Built for 3D stars;
+ * 2D stars and box stencils always use PARALLEL. */
+typedef enum {
+    STENCIL_COVER_AUTO = 0,      /* library choice (HYBRID for 3D stars)                */
+    STENCIL_COVER_PARALLEL = 1,
+    STENCIL_COVER_HYBRID = 2
+} stencil_cover;
+
 typedef struct {
     int32_t prec;     /* stencil_precision; default NATIVE for GATHER, TF32X3 for F32 MATRIXIZED */
     int32_t bc;       /* stencil_boundary; default DIRICHLET_ZERO                              */
     int32_t impl;     /* stencil_impl; default AUTO                                            */
     int32_t tb;       /* time steps fused per sweep (temporal blocking); 0 = library choice     */
-    int32_t reserved[4];
+    int32_t cover;    /* stencil_cover; default AUTO (EINVAL when out of range)                 */
+    int32_t reserved[3];
 } stencil_options;
 
 /* Plan introspection (filled by stencil_plan_info). */

@@ -47,7 +47,7 @@ class StencilError(RuntimeError):
 
 class stencil_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("bc", ctypes.c_int32), ("impl", ctypes.c_int32),
-                ("tb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("tb", ctypes.c_int32), ("cover", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class stencil_batch_info_t(ctypes.Structure):
@@ -165,12 +165,16 @@ def stencil_version() -> str:
     return lib().stencil_version().decode()
 
 
-def make_options(prec="native", bc="dirichlet", impl="auto", tb=0) -> stencil_options:
+COVERS = {"auto": 0, "parallel": 1, "hybrid": 2}
+
+
+def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto") -> stencil_options:
     o = stencil_options()
     o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     o.bc = BCS[bc] if isinstance(bc, str) else int(bc)
     o.impl = IMPLS[impl] if isinstance(impl, str) else int(impl)
     o.tb = int(tb)
+    o.cover = COVERS[cover] if isinstance(cover, str) else int(cover)
     return o
 
 
@@ -360,11 +364,11 @@ class Plan:
     """A plan for torch CUDA tensors of the plan's dtype and shape."""
 
     def __init__(self, shape, radius, kind, coeffs, dtype="f32", bc="dirichlet", impl="auto",
-                 prec="native", tb=0):
+                 prec="native", tb=0, cover="auto"):
         self.shape = tuple(int(s) for s in shape)
         self.dtype = dtype
         self.handle = stencil_plan_create(self.shape, radius, kind, coeffs, dtype,
-                                          make_options(prec, bc, impl, tb))
+                                          make_options(prec, bc, impl, tb, cover))
         self.info = stencil_plan_info(self.handle)
 
     def apply(self, x, out=None, steps=1, stream=None):

@@ -135,6 +135,8 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     if (o.impl < STENCIL_IMPL_AUTO || o.impl > STENCIL_IMPL_MATRIXIZED)
         return fail(STENCIL_EINVAL, "impl out of range");
     if (o.tb < 0 || o.tb > 16) return fail(STENCIL_EINVAL, "tb must be in 0..16");
+    if (o.cover < STENCIL_COVER_AUTO || o.cover > STENCIL_COVER_HYBRID)
+        return fail(STENCIL_EINVAL, "cover out of range");
     const int W = 2 * radius + 1;
     int64_t nco = 1, points = 1;
     for (int d = 0; d < ndim; ++d) {
@@ -188,6 +190,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     req.cg = p->cg.data();
     req.prec = (prec == STENCIL_PREC_NATIVE) ? STENCIL_PREC_TF32X3 : prec;
     req.tb = o.tb;
+    req.cover = o.cover;
     const bool mx_ok = (o.impl != STENCIL_IMPL_GATHER) && mx_supported(req, &why);
     const bool want_mx = (o.impl == STENCIL_IMPL_MATRIXIZED) || (prec != STENCIL_PREC_NATIVE);
     if (want_mx && !mx_ok) return fail(STENCIL_EUNSUPPORTED, "matrixized kernel not available: " + why);

@@ -540,6 +540,10 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         return false;
     }
     if (q.ndim == 3) return mx3d_supported(q, why);
+    if (q.cover == STENCIL_COVER_HYBRID) {
+        if (why) *why = "the hybrid line cover is built for 3D stars";
+        return false;
+    }
     if (q.prec < STENCIL_PREC_TF32 || q.prec > STENCIL_PREC_BF16X3) {
         if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2 or BF16X3";
         return false;

@@ -21,6 +21,7 @@ struct MxRequest {
     const double* cg = nullptr;  // host, dense C^g
     int prec = STENCIL_PREC_TF32X3;
     int tb = 0;                   // 0 = library choice
+    int cover = 0;                // stencil_cover (stars only)
 };
 
 struct MxPlan {

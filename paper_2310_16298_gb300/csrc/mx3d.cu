@@ -48,12 +48,15 @@ constexpr int kSmemBudget = 227 * 1024;
 constexpr int kChunk = 32;  // output planes per work unit
 
 // Coefficient lines of a 3D stencil: (a = z offset, b = y offset) pairs that
-// carry weights.  Box: all (2R+1)^2 pairs.  Star: (a, R) for a != R and
-// (R, b) for every b; the centre weight sits on line (R, R).
-template <int R, bool STAR>
+// carry weights.  Box: all (2R+1)^2 pairs.  Star, parallel cover: (a, R) for
+// a != R and (R, b) for every b; the centre weight sits on line (R, R).
+// Star, hybrid cover (HYB): two tensor-core lines, the contiguous-axis line
+// (R, R) and an identity band that hands the input rows to the epilogue, which
+// applies the 4R off-axis weights to them on the CUDA cores.
+template <int R, bool STAR, bool HYB = false>
 struct Lines3 {
     static constexpr int W = 2 * R + 1;
-    static constexpr int L = STAR ? (4 * R + 1) : W * W;
+    static constexpr int L = HYB ? 2 : STAR ? (4 * R + 1) : W * W;
     __host__ __device__ static constexpr int a(int l) {
         return STAR ? (l < R ? l : (l < R + W ? R : l - W + 1)) : l / W;
     }
@@ -102,13 +105,15 @@ struct MxArgs3D {
     uint32_t bop_bytes;
     uint32_t bpart_bytes;
     int nprod;
+    float sw[12];         // hybrid cover: z weights (a != R), then y weights (b != R)
 };
 
-template <int R, bool STAR, int NB, bool BF>
+template <int R, bool STAR, int NB, bool BF, bool HYB>
 __global__ void __launch_bounds__(kThreads, 1)
 mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_out,
             const MxArgs3D args) {
-    using LN = Lines3<R, STAR>;
+    using LN = Lines3<R, STAR, HYB>;
+    static_assert(!HYB || (STAR && 4 * R <= 12), "hybrid cover: star stencils, r <= 3");
     using F = OpFmt<BF>;
     constexpr int L = LN::L;
     constexpr int N = L * NB;
@@ -307,34 +312,69 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     }
                     ptx::tc_fence_after();
                     const uint32_t dbase = tmem_d + lane_off + (uint32_t)(st * N + CW * sub);
-                    // line (a, b): rows shift by b - R, target output plane slot 2R - a.
-                    // Lines are drained in batches of LB to bound live registers.
-                    constexpr int LB = (CW == 16) ? 2 : 4;
-#pragma unroll
-                    for (int l0 = 0; l0 < L; l0 += LB) {
-                        uint32_t v[LB][CW];
-#pragma unroll
-                        for (int j = 0; j < LB; ++j) {
-                            if (l0 + j < L) {
-                                if constexpr (CW == 16) {
-                                    ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((l0 + j) * NB), v[j]);
-                                } else {
-                                    ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)((l0 + j) * NB), v[j]);
-                                }
-                            }
+                    if constexpr (HYB) {
+                        // contiguous-axis line -> centre plane; identity band (the
+                        // input rows) x off-axis weights: z offsets without a row
+                        // shift, y offsets shifted by b - R rows
+                        uint32_t vx[CW], vi[CW];
+                        if constexpr (CW == 16) {
+                            ptx::tmem_ld_32x32b_x16(dbase, vx);
+                            ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)NB, vi);
+                        } else {
+                            ptx::tmem_ld_32x32b_x8(dbase, vx);
+                            ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)NB, vi);
                         }
                         ptx::tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < LB; ++j) {
-                            const int l = l0 + j;
-                            if (l < L) {
-                                const int la = LN::a(l), lb = LN::b(l);
-                                const int src = (lane + lb - R) & 31;
+                        for (int c = 0; c < CW; ++c) acc[R][c] += __uint_as_float(vx[c]);
 #pragma unroll
-                                for (int c = 0; c < CW; ++c) {
-                                    const float val = (lb == R) ? __uint_as_float(v[j][c])
-                                                                : __shfl_sync(0xffffffffu, __uint_as_float(v[j][c]), src);
-                                    acc[2 * R - la][c] += val;
+                        for (int k = 0; k < 2 * R; ++k) {
+                            const int a = k < R ? k : k + 1;
+                            const float w = args.sw[k];
+#pragma unroll
+                            for (int c = 0; c < CW; ++c) acc[2 * R - a][c] += w * __uint_as_float(vi[c]);
+                        }
+#pragma unroll
+                        for (int k = 0; k < 2 * R; ++k) {
+                            const int b = k < R ? k : k + 1;
+                            const float w = args.sw[2 * R + k];
+                            const int src = (lane + b - R) & 31;
+                            float tv[CW];
+#pragma unroll
+                            for (int c = 0; c < CW; ++c) tv[c] = __shfl_sync(0xffffffffu, __uint_as_float(vi[c]), src);
+#pragma unroll
+                            for (int c = 0; c < CW; ++c) acc[R][c] += w * tv[c];
+                        }
+                    } else {
+                        // line (a, b): rows shift by b - R, target output plane slot 2R - a.
+                        // Lines are drained in batches of LB to bound live registers.
+                        constexpr int LB = (CW == 16) ? 2 : 4;
+    #pragma unroll
+                        for (int l0 = 0; l0 < L; l0 += LB) {
+                            uint32_t v[LB][CW];
+    #pragma unroll
+                            for (int j = 0; j < LB; ++j) {
+                                if (l0 + j < L) {
+                                    if constexpr (CW == 16) {
+                                        ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((l0 + j) * NB), v[j]);
+                                    } else {
+                                        ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)((l0 + j) * NB), v[j]);
+                                    }
+                                }
+                            }
+                            ptx::tmem_wait_ld();
+    #pragma unroll
+                            for (int j = 0; j < LB; ++j) {
+                                const int l = l0 + j;
+                                if (l < L) {
+                                    const int la = LN::a(l), lb = LN::b(l);
+                                    const int src = (lane + lb - R) & 31;
+    #pragma unroll
+                                    for (int c = 0; c < CW; ++c) {
+                                        const float val = (lb == R) ? __uint_as_float(v[j][c])
+                                                                    : __shfl_sync(0xffffffffu, __uint_as_float(v[j][c]), src);
+                                        acc[2 * R - la][c] += val;
+                                    }
                                 }
                             }
                         }
@@ -400,25 +440,44 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
 
 using Mx3Kernel = void (*)(CUtensorMap, CUtensorMap, MxArgs3D);
 
-template <int R, bool STAR, bool BF>
-Mx3Kernel kernel3() {
-    return mx3d_kernel<R, STAR, tile_nb3<BF>(Lines3<R, STAR>::L), BF>;
+// Output columns per tile: tile_nb3 of the line count, except that the hybrid
+// cover's 2r+1 register plane sums stay within the register budget only at
+// 16 columns for r >= 2.
+template <bool BF>
+__host__ __device__ constexpr int nb3(int r, int lines, bool hyb) {
+    return (hyb && r >= 2) ? 16 : tile_nb3<BF>(lines);
 }
 
-Mx3Kernel kernel3_for(int r, bool star, bool bf) {
+template <int R, bool STAR, bool BF, bool HYB>
+Mx3Kernel kernel3() {
+    return mx3d_kernel<R, STAR, nb3<BF>(R, Lines3<R, STAR, HYB>::L, HYB), BF, HYB>;
+}
+
+template <int R>
+Mx3Kernel kernel3_star(bool bf, bool hyb) {
+    if (hyb) return bf ? kernel3<R, true, true, true>() : kernel3<R, true, false, true>();
+    return bf ? kernel3<R, true, true, false>() : kernel3<R, true, false, false>();
+}
+
+// Kernel for order r, star/box, BF16 (else TF32) operands, hybrid star cover.
+Mx3Kernel kernel3_for(int r, bool star, bool bf, bool hyb) {
     if (star) {
         switch (r) {
-            case 1: return bf ? kernel3<1, true, true>() : kernel3<1, true, false>();
-            case 2: return bf ? kernel3<2, true, true>() : kernel3<2, true, false>();
-            case 3: return bf ? kernel3<3, true, true>() : kernel3<3, true, false>();
+            case 1: return kernel3_star<1>(bf, hyb);
+            case 2: return kernel3_star<2>(bf, hyb);
+            case 3: return kernel3_star<3>(bf, hyb);
         }
-    } else if (r == 1) {
-        return bf ? kernel3<1, false, true>() : kernel3<1, false, false>();
+    } else if (r == 1 && !hyb) {
+        return bf ? kernel3<1, false, true, false>() : kernel3<1, false, false, false>();
     }
     return nullptr;
 }
 
-int lines3(int r, bool star) { return star ? 4 * r + 1 : (2 * r + 1) * (2 * r + 1); }
+// Tensor-core lines of a plan (hybrid star cover: the contiguous-axis line
+// and the identity band).
+int lines3(int r, bool star, bool hyb = false) {
+    return hyb ? 2 : star ? 4 * r + 1 : (2 * r + 1) * (2 * r + 1);
+}
 int line3_a(int r, bool star, int l) {
     const int W = 2 * r + 1;
     return star ? (l < r ? l : (l < r + W ? r : l - W + 1)) : l / W;
@@ -461,9 +520,14 @@ struct Mx3State {
     int in_w = 24;
     bool star = false;
     bool bf = false;
+    bool hyb = false;     // hybrid star cover
+    float sw[12] = {};    // its off-axis weights (z, then y)
     uint32_t bop_bytes = 0;
     uint32_t bpart_bytes = 0;
 };
+
+// The hybrid cover is the library's choice for 3D stars.
+bool use_hybrid(const MxRequest& q) { return q.star && q.cover != STENCIL_COVER_PARALLEL; }
 
 }  // namespace
 
@@ -476,7 +540,11 @@ bool mx3d_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "the 3D matrixized kernel handles the zero Dirichlet boundary only";
         return false;
     }
-    if (!kernel3_for(q.r, q.star, false)) {
+    if (q.cover == STENCIL_COVER_HYBRID && !q.star) {
+        if (why) *why = "the hybrid line cover applies to star stencils";
+        return false;
+    }
+    if (!kernel3_for(q.r, q.star, false, use_hybrid(q))) {
         if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27-point box";
         return false;
     }
@@ -494,18 +562,26 @@ bool mx3d_supported(const MxRequest& q, std::string* why) {
 stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     if (!mx3d_supported(q, why)) return STENCIL_EUNSUPPORTED;
     const int r = q.r, W = 2 * r + 1;
-    const int L = lines3(r, q.star);
+    const bool hyb = use_hybrid(q);
+    const int L = lines3(r, q.star, hyb);
     const bool bf = is_bf16(q.prec);
-    const int NB = bf ? tile_nb3<true>(L) : tile_nb3<false>(L);
+    const int NB = bf ? nb3<true>(r, L, hyb) : nb3<false>(r, L, hyb);
     const int KW = bf ? OpFmt<true>::window(NB) : OpFmt<false>::window(NB);
     p->nb = NB;
     std::vector<const double*> lines;
-    for (int l = 0; l < L; ++l)
-        lines.push_back(q.cg + ((size_t)line3_a(r, q.star, l) * W + line3_b(r, q.star, l)) * W);
+    std::vector<double> ident(W, 0.0);   // the identity band's weights: the row itself
+    ident[r] = 1.0;
+    if (hyb) {
+        lines.push_back(q.cg + ((size_t)r * W + r) * W);   // contiguous-axis line (r, r)
+        lines.push_back(ident.data());
+    } else {
+        for (int l = 0; l < L; ++l)
+            lines.push_back(q.cg + ((size_t)line3_a(r, q.star, l) * W + line3_b(r, q.star, l)) * W);
+    }
     uint32_t bpart = 0;
     std::vector<unsigned char> ops = pack_bands(r, lines, NB, KW, bf, &bpart);
     p->n_lines = L;
-    p->n_scalar = 0;
+    p->n_scalar = hyb ? 4 * r : 0;
     p->operand_bytes = ops.size();
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {
@@ -518,6 +594,13 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     st->in_w = KW;
     st->star = q.star;
     st->bf = bf;
+    st->hyb = hyb;
+    if (hyb)
+        for (int k = 0; k < 2 * r; ++k) {
+            const int o = k < r ? k : k + 1;   // offsets 0..2r except r
+            st->sw[k] = (float)q.cg[((size_t)o * W + r) * W + r];            // z offset o
+            st->sw[2 * r + k] = (float)q.cg[((size_t)r * W + o) * W + r];    // y offset o
+        }
     st->bop_bytes = (uint32_t)p->operand_bytes;
     st->bpart_bytes = bpart;
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
@@ -527,7 +610,7 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess && st->bop_bytes != (uint32_t)bop_bytes3(NB, L, bf)) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel3_for(r, q.star, bf), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(kernel3_for(r, q.star, bf, hyb), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem_bytes_3d(NB, L, bf));
     p->tmap_storage = st;
     if (e != cudaSuccess) {
@@ -582,8 +665,9 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb / kSubs, kSlabRows - 2 * p.r))
         return cudaErrorInvalidValue;
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
-    const int smem = smem_bytes_3d(st->nb, lines3(p.r, st->star), st->bf);
-    kernel3_for(p.r, st->star, st->bf)<<<grid, kThreads, smem, s>>>(map, map_out, a);
+    for (int k = 0; k < 12; ++k) a.sw[k] = st->sw[k];
+    const int smem = smem_bytes_3d(st->nb, lines3(p.r, st->star, st->hyb), st->bf);
+    kernel3_for(p.r, st->star, st->bf, st->hyb)<<<grid, kThreads, smem, s>>>(map, map_out, a);
     return cudaGetLastError();
 }
 

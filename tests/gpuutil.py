@@ -24,7 +24,7 @@ def torch_dtype(dtype):
 
 def run(field: np.ndarray, r: int, kind: str, cg: np.ndarray, dtype: str, bc: str, steps: int,
         impl: str = "gather", prec: str = "native", tb: int = 0, check_guard: bool = True,
-        alias: bool = False):
+        alias: bool = False, cover: str = "auto"):
     """Returns (result as float64 ndarray, plan info)."""
     import torch
     td = torch_dtype(dtype)
@@ -34,7 +34,7 @@ def run(field: np.ndarray, r: int, kind: str, cg: np.ndarray, dtype: str, bc: st
     x = buf_in[GUARD:GUARD + n]
     x.copy_(torch.from_numpy(np.ascontiguousarray(field).ravel()).to(td))
     y = x if alias else buf_out[GUARD:GUARD + n]
-    plan = sx.stencil_plan_create(field.shape, r, kind, cg, dtype, sx.make_options(prec, bc, impl, tb))
+    plan = sx.stencil_plan_create(field.shape, r, kind, cg, dtype, sx.make_options(prec, bc, impl, tb, cover))
     try:
         info = sx.stencil_plan_info(plan)
         stream = torch.cuda.current_stream()

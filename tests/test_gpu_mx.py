@@ -99,6 +99,36 @@ def test_mx_3d(prec, kind, r, shape):
     check(got, oracle.gather(a, r, cg, "dirichlet", steps), TOL[prec], f"mx 3d {kind} r={r} {shape} {prec}")
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("cover", ["parallel", "hybrid"])
+def test_mx_3d_star_covers(prec, r, cover):
+    """Both line covers of a 3D star (Tables cls-3d): the parallel cover puts
+    every line on the tensor cores, the hybrid cover only the contiguous-axis
+    line (plus an identity band) and applies the 4r off-axis weights on the
+    CUDA cores; both match the oracle."""
+    shape = (38, 70, 52)
+    a, cg = problem(3, shape, r, "star", seed=60 + r)
+    steps = 3
+    got, info = run(a, r, "star", cg, "f32", "dirichlet", steps, impl="matrixized", prec=prec, cover=cover)
+    assert info["impl"] == 2 and info["device_error"] == 0
+    assert info["n_scalar"] == (4 * r if cover == "hybrid" else 0)
+    check(got, oracle.gather(a, r, cg, "dirichlet", steps), TOL[prec], f"mx 3d star r={r} {cover} {prec}")
+
+
+def test_mx_hybrid_cover_only_for_3d_stars():
+    import paper_2310_16298_gb300 as sx
+    cg3 = np.ones((3, 3, 3)) / 27
+    with pytest.raises(sx.StencilError) as ei:
+        sx.stencil_plan_create((16, 16, 16), 1, "box", cg3, "f32", sx.make_options(impl="matrixized", cover="hybrid"))
+    assert ei.value.status == sx.EUNSUPPORTED
+    cg2 = np.zeros((3, 3))
+    cg2[1, :] = cg2[:, 1] = 0.2
+    with pytest.raises(sx.StencilError) as ei:
+        sx.stencil_plan_create((64, 64), 1, "star", cg2, "f32", sx.make_options(impl="matrixized", cover="hybrid"))
+    assert ei.value.status == sx.EUNSUPPORTED
+
+
 def test_mx_3d_symmetric_closed_form():
     """Symmetric 7-point star on a Dirichlet sine mode: lam^T times the mode."""
     shape = (36, 40, 48)

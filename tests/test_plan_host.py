@@ -98,6 +98,13 @@ def test_plan_create_rejects_invalid_problems(args, msg):
     assert msg in str(ei.value)
 
 
+def test_plan_create_rejects_unknown_cover():
+    with pytest.raises(sx.StencilError) as ei:
+        sx.stencil_plan_create((16, 16), 1, "box", np.ones((3, 3)), "f32", sx.make_options(cover=7))
+    assert ei.value.status == sx.EINVAL
+    assert "cover" in str(ei.value)
+
+
 def test_plan_create_rejects_tensor_precision_for_f64():
     with pytest.raises(sx.StencilError) as ei:
         sx.stencil_plan_create((16, 16), 1, "box", np.ones((3, 3)), "f64", sx.make_options(prec="tf32"))
