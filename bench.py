@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
                     choices=["box25-8192", "star7-512", "box27-512", "sine7-512", "sine27-512", "jacobi-256",
-                             "batch-1024", "serve-2000"])
+                             "batch-1024", "serve-2000", "error-growth"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
@@ -351,6 +351,41 @@ def run_batch_workload(args):
 
 
 # ------------------------------------------------------------------ serving workload
+def run_error_growth(args):
+    """Error against the FP64 oracle (full grid) after 10, 100 and 1000 steps
+    for every precision mode of the matrixized kernel and for the FP32 gather
+    kernel: 2D r=2 box, 512^2 FP32, periodic, the coefficients and field of
+    the 8192^2 workload's recipe."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_2310_16298_gb300 as sx
+    import stencil_inputs as si
+    import oracle
+    torch.cuda.set_device(local)
+    p = si.box25_8192("f32", 1, args.side or 512)
+    field = p.field()
+    x = torch.tensor(field, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    modes = [("gather", "native"), ("matrixized", "tf32x3"), ("matrixized", "bf16x3"), ("matrixized", "bf16x2"),
+             ("matrixized", "tf32"), ("matrixized", "bf16")]
+    table = {}
+    for steps in (10, 100, 1000):
+        ref = oracle.gather(field, p.r, p.coeffs, p.bc, steps)
+        for impl, prec in modes:
+            plan = sx.Plan(p.shape, p.r, p.kind, p.coeffs, "f32", bc=p.bc, impl=impl, prec=prec)
+            plan.apply(x, y, steps)
+            torch.cuda.synchronize()
+            l2, mx = oracle.error_norms(y.double().cpu().numpy(), ref)
+            table.setdefault(f"{impl}-{prec}", {})[str(steps)] = {"rel_l2": l2, "rel_max": mx}
+            plan.close()
+    line = {"metric": "rel-L2 / rel-max error vs the FP64 oracle after T steps", "value": None, "unit": "",
+            "workload": f"2D box r=2 (25-point) {p.shape[0]}x{p.shape[1]} FP32, periodic, full-grid comparison",
+            "errors": table}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving_workload(args):
     """Poisson arrivals of mixed stencil solves (70% 2D 128^2..4096^2 r=1..3
     star|box, 30% 3D 64^3..384^3 7/27-point, 10% FP64, steps 10..500) served
@@ -443,6 +478,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "serve-2000":
         return run_serving_workload(args)
+    if args.workload == "error-growth":
+        return run_error_growth(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_16298_gb300 as sx
