@@ -336,6 +336,7 @@ def run_batch_workload(args):
                                        f"log-uniform in [64, 2048], steps uniform in [20, 200], FP32, zero Dirichlet; "
                                        f"one CUDA-graph replay of packed persistent launches per step",
                            "points": npts, "updates_per_run": info["updates"], "tb": info["tb"],
+                           "tile_shape": ["64x128", "32x64"][info["tile_shape"]],
                            "launches_per_run": info["launches"], "tiles_per_run": info["tiles"],
                            "create_s": create_s, "parallelism": f"replicas x{world}",
                            "l2_policy": f"{npts * 8 / 2**30:.1f} GiB of grids per run > L2; no flush"},

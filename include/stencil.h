@@ -223,16 +223,21 @@ STENCIL_API const char *stencil_last_error(void);
  * both cases the whole launch sequence is captured once in a CUDA graph and
  * replayed by stencil_batch_launch.
  *
- * stencil_batch_create -- build the schedule and the graph.
- *   tb  time steps per launch; 0 = autotune: each depth 1..4 that fits shared
- *       memory is timed on one launch of this batch (reading d_in, writing the
- *       plans' scratch grids) and the fastest per step is kept (cached per
- *       order, kind, dtype and batch size class).  d_in must hold the inputs
- *       when create is called if tb = 0.
+ * stencil_batch_create_ex -- build the schedule and the graph.
+ *   tb          time steps per launch (1..8); 0 = autotune.
+ *   tile_shape  output tile of the packed launches: 0 = 64 x 128,
+ *               1 = 32 x 64 (rows x columns); -1 = autotune.
+ *   The autotuner times one launch of this batch (reading d_in, writing the
+ *   plans' scratch grids) for each (tile shape, depth 1..4) pair left open
+ *   that fits shared memory, and keeps the pair fastest per time step (cached
+ *   per order, kind, dtype, batch size class and the fixed values).  d_in must
+ *   hold the inputs when create is called if anything is autotuned.  Both
+ *   values are ignored when the batch is not packed.
  *   The arrays plans/d_in/d_out/steps are copied; the buffers must stay valid
  *   while the batch exists.  d_in[i] == d_out[i] is allowed.
- * Errors: EINVAL (NULL or negative entries), EUNSUPPORTED (tb too deep for
- * shared memory), ENOMEM / ECUDA.
+ * stencil_batch_create -- stencil_batch_create_ex with tile_shape = -1.
+ * Errors: EINVAL (NULL or negative entries, tb or tile_shape out of range),
+ * EUNSUPPORTED (tb too deep for shared memory), ENOMEM / ECUDA.
  */
 typedef struct stencil_batch_s *stencil_batch_t;
 
@@ -240,11 +245,14 @@ typedef struct {
     int32_t packed;    /* 1: problems share persistent launches                */
     int32_t tb;        /* time steps per launch                                */
     int32_t launches;  /* packed launches per run (-1 when not packed)         */
-    int32_t reserved;
+    int32_t tile_shape;/* tile shape of the packed launches (-1: not packed)   */
     int64_t tiles;     /* output tiles processed per run (packed)              */
     int64_t updates;   /* stencil updates per run (sum of points x steps)      */
 } stencil_batch_info_t;
 
+STENCIL_API stencil_status stencil_batch_create_ex(stencil_batch_t *out, int n, const stencil_plan_t *plans,
+                                                   const void *const *d_in, void *const *d_out,
+                                                   const int64_t *steps, int32_t tb, int32_t tile_shape);
 STENCIL_API stencil_status stencil_batch_create(stencil_batch_t *out, int n, const stencil_plan_t *plans,
                                                 const void *const *d_in, void *const *d_out, const int64_t *steps,
                                                 int32_t tb);

@@ -52,7 +52,7 @@ class stencil_options(ctypes.Structure):
 
 class stencil_batch_info_t(ctypes.Structure):
     _fields_ = [("packed", ctypes.c_int32), ("tb", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tiles", ctypes.c_int64), ("updates", ctypes.c_int64)]
+                ("tile_shape", ctypes.c_int32), ("tiles", ctypes.c_int64), ("updates", ctypes.c_int64)]
 
 
 class stencil_request(ctypes.Structure):
@@ -102,6 +102,9 @@ _SIGS = {
                                          ctypes.POINTER(_P), _I64P, _P]),
     "stencil_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                             ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.c_int32]),
+    "stencil_batch_create_ex": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                               ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.c_int32,
+                                               ctypes.c_int32]),
     "stencil_batch_launch": (ctypes.c_int, [_P, _P]),
     "stencil_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(stencil_batch_info_t)]),
     "stencil_batch_destroy": (ctypes.c_int, [_P]),
@@ -251,6 +254,19 @@ def stencil_batch_create(plans: Sequence[int], d_in: Sequence[int], d_out: Seque
     S = np.ascontiguousarray(steps, dtype=np.int64)
     _check(lib().stencil_batch_create(ctypes.byref(h), n, P, I, O, S.ctypes.data_as(_I64P), int(tb)),
            "stencil_batch_create")
+    return h.value
+
+
+def stencil_batch_create_ex(plans: Sequence[int], d_in: Sequence[int], d_out: Sequence[int],
+                            steps: Sequence[int], tb: int = 0, tile_shape: int = -1) -> int:
+    n = len(plans)
+    h = _P()
+    P = (_P * n)(*plans)
+    I = (_P * n)(*d_in)
+    O = (_P * n)(*d_out)
+    S = np.ascontiguousarray(steps, dtype=np.int64)
+    _check(lib().stencil_batch_create_ex(ctypes.byref(h), n, P, I, O, S.ctypes.data_as(_I64P), int(tb),
+                                         int(tile_shape)), "stencil_batch_create_ex")
     return h.value
 
 

@@ -20,6 +20,7 @@ struct stencil_batch_s {
     int n = 0;
     bool packed = false;  // one persistent kernel per launch (else per-problem sweeps)
     int tb = 1;
+    int shape = 0;        // batch tile shape of the packed launches
     int launches = 0;
     int64_t tiles = 0;
     int64_t updates = 0;
@@ -48,9 +49,9 @@ struct Schedule {
 // Per-problem ping-pong: sweep k of problem i goes from src to dst so that
 // the last sweep writes d_out[i] and no sweep reads what it writes.
 void build_schedule(int n, const stencil_plan_t* plans, const void* const* d_in, void* const* d_out,
-                    const int64_t* steps, int tb, Schedule* S) {
+                    const int64_t* steps, int tb, int shape, Schedule* S) {
     int ty = 0, tx = 0;
-    gather_tile_shape(2, &ty, &tx);
+    gather_batch_tile_shape(shape, &ty, &tx);
     int64_t max_sweeps = 0;
     std::vector<int64_t> sweeps(n);
     std::vector<const void*> cur(n);
@@ -131,7 +132,8 @@ stencil_status upload_tables(int n, const stencil_plan_t* plans, const Schedule&
     return STENCIL_OK;
 }
 
-cudaError_t enqueue(const stencil_plan_s* p0, const Schedule& S, void* d_tables, size_t coef_off, cudaStream_t s) {
+cudaError_t enqueue(const stencil_plan_s* p0, const Schedule& S, void* d_tables, size_t coef_off, int shape,
+                    cudaStream_t s) {
     for (const auto& c : S.copies) {
         cudaError_t e = cudaMemcpyAsync(std::get<1>(c), std::get<0>(c), std::get<2>(c), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
@@ -139,24 +141,28 @@ cudaError_t enqueue(const stencil_plan_s* p0, const Schedule& S, void* d_tables,
     for (const Launch& L : S.launches) {
         cudaError_t e = gather_batch_sweep(p0->f64, p0->star, p0->r,
                                            (const BatchProblem*)((char*)d_tables + L.table_off), L.nprob, L.tiles,
-                                           (const char*)d_tables + coef_off, L.max_depth, s);
+                                           (const char*)d_tables + coef_off, L.max_depth, shape, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Autotuner cache: (order, star, f64, log2 of the batch's points) -> depth.
+// Autotuner cache: (order, star, f64, log2 of the batch's points, fixed
+// depth or 0, fixed shape or -1) -> (tile shape, depth).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, bool, bool, int>, int> g_tune;
+std::map<std::tuple<int, bool, bool, int, int, int>, std::pair<int, int>> g_tune;
 
-// Time one launch of the batch's first sweep for each candidate depth (the
-// outputs go to the plans' scratch grids, the inputs are only read) and keep
-// the depth with the lowest time per time step.
-int autotune_depth(int n, const stencil_plan_t* plans, const void* const* d_in, const int64_t* steps) {
+// Time one launch of the batch's first sweep for each candidate (tile shape,
+// depth) pair -- the depth held when tb_fixed > 0, the shape when
+// shape_fixed >= 0 -- (the outputs go to the plans' scratch grids, the inputs
+// are only read) and keep the pair with the lowest time per time step.
+std::pair<int, int> autotune(int n, const stencil_plan_t* plans, const void* const* d_in, const int64_t* steps,
+                             int tb_fixed, int shape_fixed) {
     const stencil_plan_s* p0 = plans[0];
     int64_t pts = 0;
     for (int i = 0; i < n; ++i) pts += plans[i]->points;
-    const auto key = std::make_tuple(p0->r, p0->star, p0->f64, (int)std::log2((double)std::max<int64_t>(pts, 1)));
+    const auto key = std::make_tuple(p0->r, p0->star, p0->f64, (int)std::log2((double)std::max<int64_t>(pts, 1)),
+                                     tb_fixed, shape_fixed);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -168,37 +174,40 @@ int autotune_depth(int n, const stencil_plan_t* plans, const void* const* d_in, 
     std::vector<void*> scratch_out(n);
     std::vector<int64_t> one(n);
     for (int i = 0; i < n; ++i) scratch_out[i] = plans[i]->scratch;
-    int best = 1;
+    std::pair<int, int> best{shape_fixed >= 0 ? shape_fixed : 0, tb_fixed > 0 ? tb_fixed : 1};
     double best_t = 1e30;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return 1;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return best;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int tb = 1; tb <= 4; ++tb) {
-        GatherProblem g = gather_problem(p0);
-        if (gather_smem_bytes(g, tb) > (size_t)max_smem) break;
-        for (int i = 0; i < n; ++i) one[i] = std::min<int64_t>(steps[i], tb) > 0 ? tb : 0;
-        Schedule S;
-        build_schedule(n, plans, d_in, scratch_out.data(), one.data(), tb, &S);
-        S.copies.clear();
-        void* d = nullptr;
-        size_t coef_off = 0;
-        if (upload_tables(n, plans, S, p0->f64, &d, &coef_off) != STENCIL_OK) break;
-        float ms = 0.0f;
-        bool ok = enqueue(p0, S, d, coef_off, s) == cudaSuccess;  // warm-up
-        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-        for (int rep = 0; rep < 2 && ok; ++rep) ok = enqueue(p0, S, d, coef_off, s) == cudaSuccess;
-        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-        cudaFree(d);
-        if (!ok) break;
-        const double per_step = ms / (2.0 * tb);
-        if (per_step < best_t) {
-            best_t = per_step;
-            best = tb;
+    const int s_lo = shape_fixed >= 0 ? shape_fixed : 0;
+    const int s_hi = shape_fixed >= 0 ? shape_fixed : gather_batch_shapes() - 1;
+    const int t_lo = tb_fixed > 0 ? tb_fixed : 1, t_hi = tb_fixed > 0 ? tb_fixed : 4;
+    for (int shape = s_lo; shape <= s_hi; ++shape)
+        for (int tb = t_lo; tb <= t_hi; ++tb) {
+            if (gather_batch_smem_bytes(p0->f64, p0->r, tb, shape) > (size_t)max_smem) break;
+            for (int i = 0; i < n; ++i) one[i] = std::min<int64_t>(steps[i], tb) > 0 ? tb : 0;
+            Schedule S;
+            build_schedule(n, plans, d_in, scratch_out.data(), one.data(), tb, shape, &S);
+            S.copies.clear();
+            void* d = nullptr;
+            size_t coef_off = 0;
+            if (upload_tables(n, plans, S, p0->f64, &d, &coef_off) != STENCIL_OK) break;
+            float ms = 0.0f;
+            bool ok = enqueue(p0, S, d, coef_off, shape, s) == cudaSuccess;  // warm-up
+            ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+            for (int rep = 0; rep < 2 && ok; ++rep) ok = enqueue(p0, S, d, coef_off, shape, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            cudaFree(d);
+            if (!ok) break;
+            const double per_step = ms / (2.0 * tb);
+            if (per_step < best_t) {
+                best_t = per_step;
+                best = {shape, tb};
+            }
         }
-    }
     cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -218,14 +227,16 @@ void batch_free(stencil_batch_s* b) {
 
 }  // namespace
 
-extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, const stencil_plan_t* plans,
-                                               const void* const* d_in, void* const* d_out, const int64_t* steps,
-                                               int32_t tb) {
+extern "C" stencil_status stencil_batch_create_ex(stencil_batch_t* out, int n, const stencil_plan_t* plans,
+                                                  const void* const* d_in, void* const* d_out,
+                                                  const int64_t* steps, int32_t tb, int32_t tile_shape) {
     if (!out) return fail(STENCIL_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1) return fail(STENCIL_EINVAL, "n must be >= 1");
     if (!plans || !d_in || !d_out || !steps) return fail(STENCIL_EINVAL, "NULL argument");
     if (tb < 0 || tb > 8) return fail(STENCIL_EINVAL, "tb must be in 0..8");
+    if (tile_shape < -1 || tile_shape >= gather_batch_shapes())
+        return fail(STENCIL_EINVAL, "tile_shape must be -1 or in 0.." + std::to_string(gather_batch_shapes() - 1));
     for (int i = 0; i < n; ++i)
         if (!plans[i] || !d_in[i] || !d_out[i] || steps[i] < 0)
             return fail(STENCIL_EINVAL, "invalid entry " + std::to_string(i));
@@ -244,19 +255,25 @@ extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, cons
     Schedule S;
     size_t coef_off = 0;
     if (packed) {
-        b->tb = tb > 0 ? tb : autotune_depth(n, plans, d_in, steps);
-        GatherProblem g = gather_problem(p0);
+        if (tile_shape >= 0 && tb > 0) {
+            b->shape = tile_shape;
+            b->tb = tb;
+        } else {
+            const std::pair<int, int> t = autotune(n, plans, d_in, steps, tb, tile_shape);
+            b->shape = t.first;
+            b->tb = t.second;
+        }
         int dev = 0, max_smem = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (gather_smem_bytes(g, b->tb) > (size_t)max_smem)
+        if (gather_batch_smem_bytes(p0->f64, p0->r, b->tb, b->shape) > (size_t)max_smem)
             return fail(STENCIL_EUNSUPPORTED, "temporal block depth too large for shared memory");
-        build_schedule(n, plans, d_in, d_out, steps, b->tb, &S);
+        build_schedule(n, plans, d_in, d_out, steps, b->tb, b->shape, &S);
         stencil_status st = upload_tables(n, plans, S, p0->f64, &b->d_tables, &coef_off);
         if (st != STENCIL_OK) return st;
         // set the kernel's attributes outside the capture (a launch of no tiles)
         e = gather_batch_sweep(p0->f64, p0->star, p0->r, (const BatchProblem*)b->d_tables, 0, 0, b->d_tables,
-                               b->tb, b->cap);
+                               b->tb, b->shape, b->cap);
         if (e != cudaSuccess) return cuda_fail(e, "batched kernel set-up");
         b->launches = (int)S.launches.size();
         b->tiles = S.tiles;
@@ -266,7 +283,7 @@ extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, cons
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     stencil_status st = STENCIL_OK;
     if (packed) {
-        e = enqueue(p0, S, b->d_tables, coef_off, b->cap);
+        e = enqueue(p0, S, b->d_tables, coef_off, b->shape, b->cap);
         if (e != cudaSuccess) st = cuda_fail(e, "batched sweep launch");
     } else {
         for (int i = 0; i < n && st == STENCIL_OK; ++i)
@@ -287,6 +304,12 @@ extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, cons
     return STENCIL_OK;
 }
 
+extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, const stencil_plan_t* plans,
+                                               const void* const* d_in, void* const* d_out, const int64_t* steps,
+                                               int32_t tb) {
+    return stencil_batch_create_ex(out, n, plans, d_in, d_out, steps, tb, -1);
+}
+
 extern "C" stencil_status stencil_batch_launch(stencil_batch_t b, stencil_stream_t stream) {
     if (!b) return fail(STENCIL_EINVAL, "NULL batch");
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
@@ -300,6 +323,7 @@ extern "C" stencil_status stencil_batch_info(stencil_batch_t b, stencil_batch_in
     info->packed = b->packed ? 1 : 0;
     info->tb = b->tb;
     info->launches = b->launches;
+    info->tile_shape = b->packed ? b->shape : -1;
     info->tiles = b->tiles;
     info->updates = b->updates;
     return STENCIL_OK;

@@ -277,6 +277,12 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
 // Tile shapes.
 constexpr int k2BY = 8, k2TX = 128, k2TY = 64;
 constexpr int k3BY = 8, k3TX = 32, k3TY = 16, k3TZ = 8;
+// Tile shapes of the batched kernel (rows x columns), chosen per batch by the
+// autotuner: the single-grid shape, and a smaller one that wastes less of the
+// ragged edge tiles of small problems.
+constexpr int kBatchShapes = 2;
+constexpr int kBatchTY[kBatchShapes] = {64, 32};
+constexpr int kBatchTX[kBatchShapes] = {128, 64};
 
 template <typename T>
 size_t gather_smem_bytes_t(int ndim, int r, int tb) {
@@ -335,11 +341,18 @@ cudaError_t dispatch_r(const GatherProblem& p, const void* in, void* out, int tb
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int R, bool STAR>
+template <typename T>
+size_t batch_smem_bytes_t(int r, int tb, int shape) {
+    const int H = r * tb;
+    const int nb = tb > 1 ? 2 : 1;
+    return (size_t)(nb * (kBatchTY[shape] + 2 * H) + kRS) * (kBatchTX[shape] + 2 * H) * sizeof(T);
+}
+
+template <typename T, int R, bool STAR, int S>
 cudaError_t launch_batch(const BatchProblem* probs, int nprob, int total_tiles, const void* coef, int max_tb,
                          int grid, cudaStream_t s) {
-    const size_t smem = gather_smem_bytes_t<T>(2, R, max_tb);
-    auto kern = gather2d_batch_kernel<T, R, STAR, k2BY, k2TX, k2TY>;
+    const size_t smem = batch_smem_bytes_t<T>(R, max_tb, S);
+    auto kern = gather2d_batch_kernel<T, R, STAR, k2BY, kBatchTX[S], kBatchTY[S]>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {
@@ -355,30 +368,44 @@ cudaError_t launch_batch(const BatchProblem* probs, int nprob, int total_tiles, 
     return cudaGetLastError();
 }
 
-template <typename T, bool STAR>
-cudaError_t dispatch_batch(int r, const BatchProblem* probs, int nprob, int total_tiles, const void* coef,
-                           int max_tb, int grid, cudaStream_t s) {
+template <typename T, bool STAR, int S>
+cudaError_t dispatch_batch_r(int r, const BatchProblem* probs, int nprob, int total_tiles, const void* coef,
+                             int max_tb, int grid, cudaStream_t s) {
     switch (r) {
-        case 1: return launch_batch<T, 1, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
-        case 2: return launch_batch<T, 2, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
-        case 3: return launch_batch<T, 3, STAR>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+        case 1: return launch_batch<T, 1, STAR, S>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+        case 2: return launch_batch<T, 2, STAR, S>(probs, nprob, total_tiles, coef, max_tb, grid, s);
+        case 3: return launch_batch<T, 3, STAR, S>(probs, nprob, total_tiles, coef, max_tb, grid, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <typename T, bool STAR>
+cudaError_t dispatch_batch(int r, const BatchProblem* probs, int nprob, int total_tiles, const void* coef,
+                           int max_tb, int shape, cudaStream_t s) {
+    if (shape == 1) return dispatch_batch_r<T, STAR, 1>(r, probs, nprob, total_tiles, coef, max_tb, 0, s);
+    return dispatch_batch_r<T, STAR, 0>(r, probs, nprob, total_tiles, coef, max_tb, 0, s);
 }
 
 }  // namespace
 
 cudaError_t gather_batch_sweep(bool f64, bool star, int r, const BatchProblem* d_probs, int nprob, int total_tiles,
-                               const void* d_coef, int max_tb, cudaStream_t s) {
-    if (f64) return star ? dispatch_batch<double, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s)
-                         : dispatch_batch<double, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s);
-    return star ? dispatch_batch<float, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s)
-                : dispatch_batch<float, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, 0, s);
+                               const void* d_coef, int max_tb, int shape, cudaStream_t s) {
+    if (shape < 0 || shape >= kBatchShapes) return cudaErrorInvalidValue;
+    if (f64) return star ? dispatch_batch<double, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, shape, s)
+                         : dispatch_batch<double, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, shape, s);
+    return star ? dispatch_batch<float, true>(r, d_probs, nprob, total_tiles, d_coef, max_tb, shape, s)
+                : dispatch_batch<float, false>(r, d_probs, nprob, total_tiles, d_coef, max_tb, shape, s);
 }
 
-void gather_tile_shape(int ndim, int* ty, int* tx) {
-    *ty = ndim == 2 ? k2TY : k3TY;
-    *tx = ndim == 2 ? k2TX : k3TX;
+int gather_batch_shapes() { return kBatchShapes; }
+
+void gather_batch_tile_shape(int shape, int* ty, int* tx) {
+    *ty = kBatchTY[shape];
+    *tx = kBatchTX[shape];
+}
+
+size_t gather_batch_smem_bytes(bool f64, int r, int tb, int shape) {
+    return f64 ? batch_smem_bytes_t<double>(r, tb, shape) : batch_smem_bytes_t<float>(r, tb, shape);
 }
 
 size_t gather_smem_bytes(const GatherProblem& p, int tb) {

@@ -35,12 +35,15 @@ struct BatchProblem {
     int pad;
 };
 
-// Advance every listed problem by its depth in one persistent launch.
+// Advance every listed problem by its depth in one persistent launch with
+// batch tile shape `shape` (0 .. gather_batch_shapes()-1).
 // d_probs: device array sorted by tile0; d_coef: (2r+1)^2 entries per row.
 cudaError_t gather_batch_sweep(bool f64, bool star, int r, const BatchProblem* d_probs, int nprob, int total_tiles,
-                               const void* d_coef, int max_tb, cudaStream_t s);
-// Output tile of the 2D/3D gather kernels (rows, columns).
-void gather_tile_shape(int ndim, int* ty, int* tx);
+                               const void* d_coef, int max_tb, int shape, cudaStream_t s);
+int gather_batch_shapes();
+// Output tile (rows, columns) and shared memory of a batch tile shape.
+void gather_batch_tile_shape(int shape, int* ty, int* tx);
+size_t gather_batch_smem_bytes(bool f64, int r, int tb, int shape);
 
 // Uniform[lo, hi) SplitMix64 field (elements offset .. offset+count-1 of the
 // seed's stream), rounded to the storage type.

@@ -28,7 +28,7 @@ def make_batch(n, seed, rmix=False):
     return probs
 
 
-def run_batch(probs, tb=0, alias_every=5, launches=1):
+def run_batch(probs, tb=0, alias_every=5, launches=1, tile_shape=-1):
     import torch
     plans, ins, outs, keep = [], [], [], []
     for i, (a, cg, steps, r) in enumerate(probs):
@@ -39,7 +39,11 @@ def run_batch(probs, tb=0, alias_every=5, launches=1):
         ins.append(x.data_ptr())
         outs.append(y.data_ptr())
     torch.cuda.synchronize()
-    b = sx.stencil_batch_create(plans, ins, outs, [p[2] for p in probs], tb)
+    steps = [p[2] for p in probs]
+    if tile_shape < 0:
+        b = sx.stencil_batch_create(plans, ins, outs, steps, tb)
+    else:
+        b = sx.stencil_batch_create_ex(plans, ins, outs, steps, tb, tile_shape)
     info = sx.stencil_batch_info(b)
     s = torch.cuda.current_stream().cuda_stream
     sx.stencil_batch_launch(b, s)
@@ -82,10 +86,32 @@ def test_batch_equals_alone_and_oracle(tb):
             assert np.array_equal(g, a)
 
 
+@pytest.mark.parametrize("tile_shape,tb", [(0, 2), (1, 0), (1, 1), (1, 3)])
+def test_batch_tile_shapes_equal_alone_and_oracle(tile_shape, tb):
+    """Each batch tile shape (64 x 128 and 32 x 64 outputs) gives every problem
+    the same result as running it alone, with its ragged edge tiles."""
+    probs = make_batch(30, seed=11)
+    got, info = run_batch(probs, tb=tb, tile_shape=tile_shape)
+    assert info["packed"] == 1 and info["tile_shape"] == tile_shape
+    if tb:
+        assert info["tb"] == tb
+    for (a, cg, steps, r), g in zip(probs, got):
+        assert np.array_equal(g, run_alone(a, cg, steps, r))
+        if steps:
+            l2, mx = oracle.error_norms(g, oracle.gather(a, r, cg, "dirichlet", steps))
+            assert l2 <= 1e-5 and mx <= 1e-5
+
+
+def test_batch_autotune_reports_a_valid_shape():
+    probs = make_batch(8, seed=12)
+    _, info = run_batch(probs, tb=0)
+    assert info["packed"] == 1 and info["tile_shape"] in (0, 1) and 1 <= info["tb"] <= 4
+
+
 def test_batch_mixed_orders_not_packed():
     probs = make_batch(12, seed=8, rmix=True)
     got, info = run_batch(probs, tb=0)
-    assert info["packed"] == 0
+    assert info["packed"] == 0 and info["tile_shape"] == -1
     for (a, cg, steps, r), g in zip(probs, got):
         assert np.array_equal(g, run_alone(a, cg, steps, r))
 

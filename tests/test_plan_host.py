@@ -111,6 +111,13 @@ def test_plan_create_rejects_tensor_precision_for_f64():
     assert ei.value.status == sx.EINVAL
 
 
+@pytest.mark.parametrize("tb,tile_shape", [(9, -1), (-1, 0), (0, 2), (1, -2)])
+def test_batch_create_rejects_out_of_range_depth_and_shape(tb, tile_shape):
+    # argument checks come before any plan is dereferenced or any device call
+    with pytest.raises(sx.StencilError):
+        sx.stencil_batch_create_ex([1], [1], [1], [1], tb, tile_shape)
+
+
 def test_unknown_ticket_is_rejected():
     assert sx.stencil_poll(123456789) == sx.EINVAL
     assert sx.stencil_wait(123456789, 0) == sx.EINVAL
