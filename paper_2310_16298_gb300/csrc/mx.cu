@@ -34,7 +34,10 @@
 //    quarter is loaded as two 32-row boxes through row-parity tensor maps
 //    (even rows, odd rows), so a warp reads consecutive rows (no bank
 //    conflicts) and every lane's two rows sit in the same smem slot.
-//  * warp 1: MMA issuer (one elected thread).
+//  * warps 1 and 18: MMA issuers (one thread each), alternating items.  A
+//    thread issuing tcgen05.mma is held at the tensor pipe's rate, so with
+//    one issuer the pipe drains while that thread waits on the next item's
+//    barriers; with two, one issuer's waits overlap the other's MMAs.
 //  * warps 2..9: split warps, one per (quarter, row parity): input rows ->
 //    TF32 hi/lo (or BF16 parts) -> tensor memory (tcgen05.st).
 //  * warps 10..17: epilogue warps, one per (quarter, output parity): tensor
@@ -77,7 +80,8 @@ constexpr int kItems = 2;               // items (16-column blocks) per tile
 constexpr int kTw = kItems * kNb;       // output columns per tile
 constexpr int kSplitWarps = 2 * kQuarters;   // (quarter, input row parity)
 constexpr int kEpiWarps = 2 * kQuarters;     // (quarter, output row parity)
-constexpr int kThreads = 64 + 32 * (kSplitWarps + kEpiWarps);
+constexpr int kMma2Warp = 2 + kSplitWarps + kEpiWarps;   // second MMA issuer
+constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr int kMaxRawStages = 6;
 constexpr int kTmemCols = 512;
 constexpr int kSmemBudget = 227 * 1024;
@@ -260,8 +264,9 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 issued = i + 1;
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp == 1 || warp == kMma2Warp) {
+        // ------------------------------------------------ MMA issuers (items i with i % 2 == u)
+        const int u = warp == 1 ? 0 : 1;
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
             constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
@@ -270,6 +275,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             bool ok = true;
             for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x)
             for (int j = 0; j < kItems; ++j, ++i) {
+                if ((i & 1) != u) continue;
                 const int sa = i % AST;
                 const uint32_t pa = (uint32_t)(i / AST) & 1u;
                 const int st = i % DST;
@@ -345,7 +351,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             }
         }
     } else {
-        // ------------------------------------------------ epilogue: accumulators -> outputs
+        // ------------------------------------------------ epilogue: accumulators -> outputs (warps 10..17)
         const int q = warp & 3;
         const int p = (warp - 2 - kSplitWarps) >> 2;   // output row parity of this warp
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
@@ -439,7 +445,9 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     }
 
     // ---- teardown (also after an abort: every role has left its loop)
-    if (warp >= 2 + kSplitWarps && lane == 0) ptx::bulk_wait_group<0>();   // output stores complete
+    // output stores have read their staging buffers (the writes themselves
+    // are visible to later work in the stream once the grid completes)
+    if (warp >= 2 + kSplitWarps && warp < kMma2Warp && lane == 0) ptx::bulk_wait_group_read<0>();
     if (*abort_flag) {
         // Let copies and MMAs still in flight land before the CTA gives up its
         // shared and tensor memory (each wait bounded again).
@@ -447,7 +455,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             for (int k = issued - kRawStages; k < issued; ++k)
                 if (k >= 0) ptx::mbar_wait(&full[k % kRawStages], (uint32_t)(k / kRawStages) & 1u, kWaitCycles / 8);
         }
-        if (warp == 1 && lane == 0 && committed >= 0)
+        if ((warp == 1 || warp == kMma2Warp) && lane == 0 && committed >= 0)
             ptx::mbar_wait(&accf[committed % DST], (uint32_t)(committed / DST) & 1u, kWaitCycles / 8);
     }
     __syncwarp();
