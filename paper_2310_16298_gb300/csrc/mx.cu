@@ -29,6 +29,9 @@
 // r shuffles per output instead of 2r, and fewer MACs per output than one
 // lane per row.
 //
+// Tiles are handed out at run time (an atomic counter per plan, reset by the
+// last CTA to finish), so SMs that run faster take more tiles.
+//
 // Roles (one persistent CTA per SM, warp specialised):
 //  * warp 0: TMA producer.  A tile is 4 lane quarters x 64 input rows; each
 //    quarter is loaded as two 32-row boxes through row-parity tensor maps
@@ -83,6 +86,7 @@ constexpr int kEpiWarps = 2 * kQuarters;     // (quarter, output row parity)
 constexpr int kMma2Warp = 2 + kSplitWarps + kEpiWarps;   // second MMA issuer
 constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr int kMaxRawStages = 6;
+constexpr int kTileRing = 8;            // tile ids handed from the producer to the epilogue
 constexpr int kTmemCols = 512;
 constexpr int kSmemBudget = 227 * 1024;
 
@@ -123,7 +127,8 @@ __host__ __device__ constexpr int bop_bytes() {
 }
 template <int R, bool BF>
 __host__ __device__ constexpr int smem_fixed() {
-    return 1024 /*align slack*/ + out_bytes() + bop_bytes<R, BF>() + 8 * (2 * kMaxRawStages + 16);
+    return 1024 /*align slack*/ + out_bytes() + bop_bytes<R, BF>() + 8 * (2 * kMaxRawStages + 16) +
+           8 * 2 * kTileRing + 4 * (kTileRing + kMaxRawStages + 8);
 }
 template <int R, bool BF>
 __host__ __device__ constexpr int raw_stages() {
@@ -138,6 +143,7 @@ struct MxArgs2D {
     const float* in;           // source grid (periodic halo fix-up reads it directly)
     const void* bops;          // block operands [part][kchunk][block*16 + q][16 bytes]
     unsigned int* err;         // device error word (host-mapped)
+    int* sched;                // [0] next tile to hand out, [1] CTAs finished (both 0 between launches)
     int ny, nx;
     int bc, nparts;            // operand parts of the input split (1..3)
     int tiles_x, tiles_total;
@@ -204,8 +210,13 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     uint64_t* accf = aempty + AST;                  // [DST] accumulator set ready
     uint64_t* acce = accf + DST;                    // [DST] accumulator set drained
     uint64_t* bop_bar = acce + DST;
-    uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
+    uint64_t* tq_full = bop_bar + 1;                // [kTileRing] tile id written
+    uint64_t* tq_empty = tq_full + kTileRing;       // [kTileRing] tile id read by the epilogue warps
+    uint32_t* tmem_slot = (uint32_t*)(tq_empty + kTileRing);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* tile_ring = abort_flag + 1;       // [kTileRing] tile ids (-1: no more tiles)
+    volatile int* stage_tile = tile_ring + kTileRing;   // [kRawStages] tile of each input stage
+    volatile int* a_tile = stage_tile + kMaxRawStages;  // [AST] tile of each A stage (-1: end)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -224,6 +235,10 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             ptx::mbar_init(&acce[a], kEpiWarps);
         }
         ptx::mbar_init(bop_bar, 1);
+        for (int k = 0; k < kTileRing; ++k) {
+            ptx::mbar_init(&tq_full[k], 1);
+            ptx::mbar_init(&tq_empty[k], kEpiWarps);
+        }
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -245,11 +260,22 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
         if (lane == 0) {
             ptx::mbar_arrive_expect_tx(bop_bar, args.bop_bytes);
             ptx::bulk_load(bops, args.bops, args.bop_bytes, bop_bar);
-            int i = 0;
-            for (int t = blockIdx.x; t < args.tiles_total; t += gridDim.x, ++i) {
+            for (int i = 0;; ++i) {
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
-                if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag)) break;
+                const int tq = i % kTileRing;
+                if (!wait_or_abort(&rawfree[s], ph ^ 1u, abort_flag) ||
+                    !wait_or_abort(&tq_empty[tq], ((uint32_t)(i / kTileRing) & 1u) ^ 1u, abort_flag))
+                    break;
+                int t = atomicAdd(&args.sched[0], 1);
+                if (t >= args.tiles_total) t = -1;
+                stage_tile[s] = t;
+                tile_ring[tq] = t;
+                ptx::mbar_arrive(&tq_full[tq]);
+                if (t < 0) {   // no more tiles: the split warps see the end through the stage
+                    ptx::mbar_arrive(&full[s]);
+                    break;
+                }
                 const int X0 = (t % args.tiles_x) * kTw;
                 const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
                 unsigned char* dst = raw + s * RSB;
@@ -271,19 +297,14 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
             const int pr = args.nprod;
-            int i = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x)
-            for (int j = 0; j < kItems; ++j, ++i) {
-                if ((i & 1) != u) continue;
+            for (int i = u;; i += 2) {
                 const int sa = i % AST;
                 const uint32_t pa = (uint32_t)(i / AST) & 1u;
                 const int st = i % DST;
                 const uint32_t ph = (uint32_t)(i / DST) & 1u;
-                if (!wait_or_abort(&afull[sa], pa, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
-                    ok = false;
-                    break;
-                }
+                if (!wait_or_abort(&afull[sa], pa, abort_flag)) break;
+                if (a_tile[sa] < 0) break;   // the split warps passed the end of the tiles
+                if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
                 ptx::tc_fence_after();
                 issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
                                        args.bpart_bytes, N, idesc, pr);
@@ -297,12 +318,25 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
         const int q = warp & 3;                        // TMEM lane quarter of this warp
         const int e = (warp - 2) >> 2;                 // input row parity this warp converts
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        int i = 0, k = 0;   // items, tiles
+        int i = 0;   // items
         bool ok = true;
-        for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x, ++k) {
+        for (int k = 0; ok; ++k) {
             const int rs = k % kRawStages;
             const uint32_t rph = (uint32_t)(k / kRawStages) & 1u;
             if (!wait_or_abort(&full[rs], rph, abort_flag)) break;
+            const int t = stage_tile[rs];
+            if (t < 0) {
+                // End of the tiles: one end marker per MMA issuer through the
+                // next two A stages (the issuers take alternate items).
+                for (int e2 = 0; e2 < 2; ++e2, ++i) {
+                    const int sa = i % AST;
+                    if (!wait_or_abort(&aempty[sa], ((uint32_t)(i / AST) & 1u) ^ 1u, abort_flag)) break;
+                    if (warp == 2 && lane == 0) a_tile[sa] = -1;
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&afull[sa]);
+                }
+                break;
+            }
             const int X0 = (t % args.tiles_x) * kTw;
             const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
             const int gy = Y0 + q * G::ROWS_OUT - 2 * G::DM + 2 * lane + e;   // input row of this thread
@@ -346,6 +380,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 for (int g = 0; g < NG; ++g) split_store<BF, NP>(x[g], abase, PC, e * W + GW * g);
                 ptx::tmem_wait_st();
                 ptx::tc_fence_before();
+                if (warp == 2 && lane == 0) a_tile[sa] = t;
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&afull[sa]);
             }
@@ -365,7 +400,13 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             const int prows = P ? args.rows_odd : args.rows_even;
             int i = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < args.tiles_total && ok; t += gridDim.x)
+            for (int k = 0; ok; ++k) {
+            const int tq = k % kTileRing;
+            if (!wait_or_abort(&tq_full[tq], (uint32_t)(k / kTileRing) & 1u, abort_flag)) break;
+            const int t = tile_ring[tq];
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&tq_empty[tq]);
+            if (t < 0) break;
             for (int j = 0; j < kItems; ++j, ++i) {
                 const int st = i % DST;
                 const uint32_t ph = (uint32_t)(i / DST) & 1u;
@@ -437,6 +478,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                     }
                 }
             }
+            }
         };
         if (p == 0)
             drain(std::integral_constant<int, 0>{});
@@ -462,6 +504,13 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     if (tid == 0 && *abort_flag) atomicOr(args.err, 1u);
     ptx::tc_fence_before();
     __syncthreads();
+    if (tid == 0) {   // every producer of this CTA is done: the last CTA resets the tile counter
+        __threadfence();
+        if (atomicAdd(&args.sched[1], 1) == (int)gridDim.x - 1) {
+            atomicExch(&args.sched[0], 0);
+            atomicExch(&args.sched[1], 0);
+        }
+    }
     if (warp == 1) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, kTmemCols);
@@ -534,6 +583,7 @@ bool encode_parity_map(CUtensorMap* map, const float* base, int rows_p, int nx, 
 struct MxState {
     unsigned int* err_host = nullptr;  // host-mapped error word
     unsigned int* err_dev = nullptr;
+    int* sched = nullptr;              // device tile counter pair (zero between launches)
     int num_sms = 0;
     bool bf = false;      // BF16 operands (else TF32)
     uint32_t bop_bytes = 0;
@@ -621,6 +671,13 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     }
     *st->err_host = 0;
     p->tmap_storage = st;
+    e = cudaMalloc(&st->sched, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->sched, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) {
+        mx_plan_free(p);
+        if (why) *why = std::string("tile counter: ") + cudaGetErrorString(e);
+        return STENCIL_ENOMEM;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -643,6 +700,7 @@ void mx_plan_free(MxPlan* p) {
     MxState* st = (MxState*)p->tmap_storage;
     if (st) {
         if (st->err_host) cudaFreeHost(st->err_host);
+        if (st->sched) cudaFree(st->sched);
         delete st;
     }
     p->tmap_storage = nullptr;
@@ -668,6 +726,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.in = (const float*)src;
     a.bops = p.d_operands;
     a.err = st->err_dev;
+    a.sched = st->sched;
     a.ny = ny;
     a.nx = nx;
     a.bc = p.bc;
