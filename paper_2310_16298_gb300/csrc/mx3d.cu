@@ -41,8 +41,10 @@ constexpr int kQuarters = 4;
 constexpr int kRoleWarps = 8;
 constexpr int kSubs = 2;
 constexpr int kMathWarps = 2 * kRoleWarps;
-constexpr int kThreads = 64 + 32 * kMathWarps;
+constexpr int kMma2Warp = 2 + kMathWarps;   // second MMA issuer (items alternate between warps 1 and 18)
+constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr int kMaxRawStages = 6;
+constexpr int kUnitRing = 8;                // unit ids handed from the producer to the epilogue
 constexpr int kTmemCols = 512;
 constexpr int kSmemBudget = 227 * 1024;
 constexpr int kChunk = 32;  // output planes per work unit
@@ -85,7 +87,8 @@ __host__ __device__ constexpr int bop_bytes3(int nb, int lines, bool bf) {
     return (bf ? 3 * 2 : 2 * 4) * window3(nb, bf) * lines * nb;
 }
 __host__ __device__ constexpr int smem_fixed3(int nb, int lines, bool bf) {
-    return 1024 + out_bytes3(nb) + bop_bytes3(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16);
+    return 1024 + out_bytes3(nb) + bop_bytes3(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16) + 8 * 2 * kUnitRing +
+           4 * (kUnitRing + kMaxRawStages + 8);
 }
 __host__ __device__ constexpr int raw_stages3(int nb, int lines, bool bf) {
     return (kSmemBudget - smem_fixed3(nb, lines, bf)) / raw_stage_bytes3(raw_pitch3(window3(nb, bf))) < kMaxRawStages
@@ -99,6 +102,7 @@ __host__ __device__ constexpr int smem_bytes_3d(int nb, int lines, bool bf) {
 struct MxArgs3D {
     const void* bops;     // banded operands [part][kchunk][line*NB + q][16 bytes]
     unsigned int* err;    // device error word (host-mapped)
+    int* sched;           // [0] next unit to hand out, [1] CTAs finished (both 0 between launches)
     int nz, ny, nx;
     int nparts;           // operand parts of the input split (1..3)
     int tiles_x, tiles_y, chunks, units;
@@ -153,8 +157,13 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     uint64_t* accf = aempty + AST;             // [DST]
     uint64_t* acce = accf + DST;               // [DST]
     uint64_t* bop_bar = acce + DST;
-    uint32_t* tmem_slot = (uint32_t*)(bop_bar + 1);
+    uint64_t* uq_full = bop_bar + 1;           // [kUnitRing] unit id written
+    uint64_t* uq_empty = uq_full + kUnitRing;  // [kUnitRing] unit id read by the epilogue warps
+    uint32_t* tmem_slot = (uint32_t*)(uq_empty + kUnitRing);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* unit_ring = abort_flag + 1;               // [kUnitRing] unit ids (-1: no more units)
+    volatile int* stage_unit = unit_ring + kUnitRing;       // [kRawStages] unit of each input plane stage
+    volatile int* a_unit = stage_unit + kMaxRawStages;      // [AST] -1 marks the end for the MMA issuers
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -173,6 +182,10 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             ptx::mbar_init(&acce[a], kRoleWarps);
         }
         ptx::mbar_init(bop_bar, 1);
+        for (int k = 0; k < kUnitRing; ++k) {
+            ptx::mbar_init(&uq_full[k], 1);
+            ptx::mbar_init(&uq_empty[k], kRoleWarps);
+        }
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -201,7 +214,21 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             ptx::bulk_load(bops, args.bops, args.bop_bytes, bop_bar);
             int i = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+            for (int k = 0; ok; ++k) {
+                const int uq = k % kUnitRing;
+                if (!wait_or_abort(&uq_empty[uq], ((uint32_t)(k / kUnitRing) & 1u) ^ 1u, abort_flag)) break;
+                int u = atomicAdd(&args.sched[0], 1);
+                if (u >= args.units) u = -1;
+                unit_ring[uq] = u;
+                ptx::mbar_arrive(&uq_full[uq]);
+                if (u < 0) {   // no more units: the split warps see the end through the next stage
+                    const int s = i % kRawStages;
+                    if (wait_or_abort(&rawfree[s], ((uint32_t)(i / kRawStages) & 1u) ^ 1u, abort_flag)) {
+                        stage_unit[s] = -1;
+                        ptx::mbar_arrive(&full[s]);
+                    }
+                    break;
+                }
                 int X0, Y0, Z0;
                 unit_origin(u, X0, Y0, Z0);
                 for (int iz = 0; iz < PLANES; ++iz, ++i) {
@@ -211,6 +238,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
+                    stage_unit[s] = u;
                     unsigned char* dst = raw + s * RSB;
                     ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
 #pragma unroll
@@ -221,30 +249,27 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == kMma2Warp) {
+        // two issuers, alternating items: one issuer's barrier waits overlap the
+        // other's MMAs (a thread issuing tcgen05.mma is held at the pipe's rate)
         if (lane == 0 && wait_or_abort(bop_bar, 0, abort_flag)) {
             constexpr uint32_t idesc = ptx::instr_desc(F::kFmt, F::kFmt, 128, (uint32_t)N);
             const uint64_t b0 = ptx::smem_desc(ptx::smem_u32(bops), (uint32_t)(N * 16), 128);
             const int pr = args.nprod;
-            int i = 0;
-            bool ok = true;
-            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
-                for (int iz = 0; iz < PLANES; ++iz, ++i) {
-                    const int sa = i % AST;
-                    const uint32_t pa = (uint32_t)(i / AST) & 1u;
-                    const int st = i % DST;
-                    const uint32_t ph = (uint32_t)(i / DST) & 1u;
-                    if (!wait_or_abort(&afull[sa], pa, abort_flag) || !wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
-                                           args.bpart_bytes, N, idesc, pr);
-                    ptx::mma_commit(&aempty[sa]);
-                    ptx::mma_commit(&accf[st]);
-                    committed = i;
-                }
+            for (int i = (warp == 1 ? 0 : 1);; i += 2) {
+                const int sa = i % AST;
+                const uint32_t pa = (uint32_t)(i / AST) & 1u;
+                const int st = i % DST;
+                const uint32_t ph = (uint32_t)(i / DST) & 1u;
+                if (!wait_or_abort(&afull[sa], pa, abort_flag)) break;
+                if (a_unit[sa] < 0) break;   // the split warps passed the last unit
+                if (!wait_or_abort(&acce[st], ph ^ 1u, abort_flag)) break;
+                ptx::tc_fence_after();
+                issue_products<BF, KS>(tmem_d + (uint32_t)(st * N), tmem_a + (uint32_t)(sa * A_COLS), PC, b0,
+                                       args.bpart_bytes, N, idesc, pr);
+                ptx::mma_commit(&aempty[sa]);
+                ptx::mma_commit(&accf[st]);
+                committed = i;
             }
         }
     } else {
@@ -255,14 +280,27 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         int i = 0;
         bool ok = true;
         if (split_role) {
-            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
-                for (int iz = 0; iz < PLANES; ++iz, ++i) {
+            for (;; ++i) {
+                {
                     const int rs = i % kRawStages;
                     const uint32_t rph = (uint32_t)(i / kRawStages) & 1u;
                     const int sa = i % AST;
                     const uint32_t pa = (uint32_t)(i / AST) & 1u;
                     if (!wait_or_abort(&full[rs], rph, abort_flag) || !wait_or_abort(&aempty[sa], pa ^ 1u, abort_flag)) {
                         ok = false;
+                        break;
+                    }
+                    if (stage_unit[rs] < 0) {
+                        // end of the units: one end marker per MMA issuer (items i, i + 1)
+                        for (int e2 = 0; e2 < 2; ++e2) {
+                            const int sb = (i + e2) % AST;
+                            if (e2 == 1 &&
+                                !wait_or_abort(&aempty[sb], ((uint32_t)((i + 1) / AST) & 1u) ^ 1u, abort_flag))
+                                break;
+                            if (warp == 2 && lane == 0) a_unit[sb] = -1;
+                            __syncwarp();
+                            if (lane == 0) ptx::mbar_arrive(&afull[sb]);
+                        }
                         break;
                     }
                     ptx::tc_fence_after();
@@ -286,6 +324,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     }
                     ptx::tmem_wait_st();
                     ptx::tc_fence_before();
+                    if (warp == 2 && lane == 0) a_unit[sa] = 0;
                     __syncwarp();
                     if (lane == 0) {
                         ptx::mbar_arrive(&rawfree[rs]);
@@ -295,7 +334,13 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
             }
         } else {
             int nstore = 0;
-            for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x) {
+            for (int k = 0; ok; ++k) {
+                const int uq = k % kUnitRing;
+                if (!wait_or_abort(&uq_full[uq], (uint32_t)(k / kUnitRing) & 1u, abort_flag)) break;
+                const int u = unit_ring[uq];
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&uq_empty[uq]);
+                if (u < 0) break;
                 int X0, Y0, Z0;
                 unit_origin(u, X0, Y0, Z0);
                 float acc[2 * R + 1][CW];  // running sums of output planes z-R .. z+R
@@ -419,19 +464,28 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         }
     }
 
-    if (warp >= 2 + kRoleWarps && lane == 0) ptx::bulk_wait_group<0>();
+    // output stores have read their staging buffers (the writes are visible to
+    // later work in the stream once the grid completes)
+    if (warp >= 2 + kRoleWarps && warp < kMma2Warp && lane == 0) ptx::bulk_wait_group_read<0>();
     if (*abort_flag) {
         if (warp == 0 && lane == 0) {
             for (int k = issued - kRawStages; k < issued; ++k)
                 if (k >= 0) ptx::mbar_wait(&full[k % kRawStages], (uint32_t)(k / kRawStages) & 1u, kWaitCycles / 8);
         }
-        if (warp == 1 && lane == 0 && committed >= 0)
+        if ((warp == 1 || warp == kMma2Warp) && lane == 0 && committed >= 0)
             ptx::mbar_wait(&accf[committed % DST], (uint32_t)(committed / DST) & 1u, kWaitCycles / 8);
     }
     __syncwarp();
     if (tid == 0 && *abort_flag) atomicOr(args.err, 1u);
     ptx::tc_fence_before();
     __syncthreads();
+    if (tid == 0) {   // this CTA's producer is done: the last CTA resets the unit counter
+        __threadfence();
+        if (atomicAdd(&args.sched[1], 1) == (int)gridDim.x - 1) {
+            atomicExch(&args.sched[0], 0);
+            atomicExch(&args.sched[1], 0);
+        }
+    }
     if (warp == 1) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, kTmemCols);
@@ -515,6 +569,7 @@ bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, in
 struct Mx3State {
     unsigned int* err_host = nullptr;
     unsigned int* err_dev = nullptr;
+    int* sched = nullptr;  // device unit counter pair (zero between launches)
     int num_sms = 0;
     int nb = 16;
     int in_w = 24;
@@ -605,6 +660,8 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     st->bpart_bytes = bpart;
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&st->err_dev, st->err_host, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&st->sched, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->sched, 0, 2 * sizeof(int));
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -628,6 +685,7 @@ void mx3d_plan_free(MxPlan* p) {
     Mx3State* st = (Mx3State*)p->tmap_storage;
     if (st) {
         if (st->err_host) cudaFreeHost(st->err_host);
+        if (st->sched) cudaFree(st->sched);
         delete st;
     }
     p->tmap_storage = nullptr;
@@ -649,6 +707,7 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     memset(&a, 0, sizeof(a));
     a.bops = p.d_operands;
     a.err = st->err_dev;
+    a.sched = st->sched;
     a.nz = nz;
     a.ny = ny;
     a.nx = nx;
