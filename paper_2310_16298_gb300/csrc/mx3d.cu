@@ -15,9 +15,11 @@
 //
 // Work unit = (32-row-slab tile in y, NB columns in x, a chunk of output
 // planes in z); the unit streams its chunk plus R halo planes on either side.
-// Roles per CTA as in the 2D kernel: TMA producer warp, MMA warp, 8 split
-// warps (input plane -> TF32 hi/lo A operand in tensor memory), 8 epilogue
-// warps (tensor memory -> plane accumulators -> TMA store).
+// Roles per CTA as in the 2D kernel: TMA producer warp, two MMA issuer warps
+// (alternate input planes), 8 split warps (input plane -> TF32 hi/lo A
+// operand in tensor memory), 8 epilogue warps (tensor memory -> plane
+// accumulators -> TMA store).  Work units are handed out at run time from a
+// per-plan atomic counter that the last CTA to finish resets.
 #include <cuda.h>
 #include <string.h>
 
