@@ -162,7 +162,9 @@ STENCIL_API stencil_status stencil_plan_info(stencil_plan_t plan, stencil_plan_i
  *   steps   >= 0; 0 copies d_in to d_out.
  * Errors: EINVAL (NULL pointer, steps < 0), ECUDA (launch failure).
  * Concurrent applies of one plan must be ordered by the caller: they share
- * the plan's scratch grid.
+ * the plan's scratch grid and, for the matrixized kernels, the plan's
+ * device tile counter (tiles are handed out to the SMs at run time; the
+ * counter is back at zero when a launch ends).
  */
 STENCIL_API stencil_status stencil_apply(stencil_plan_t plan, const void *d_in, void *d_out, int64_t steps,
                              stencil_stream_t stream);
