@@ -8,6 +8,9 @@ generalised to d = 2, 3 and order r); ``sample`` returns single output points
 computed on their dependency cones.  Both run the C code in
 ``stencil_oracle.c`` (plain multiply-then-add in FP64, lexicographic term
 order).  See that file's header for the boundary conventions.
+
+``min_line_cover`` is the minimal set of axis-parallel coefficient lines of a
+2D weight pattern (Sec. 3.5), found by trying every set of row lines.
 """
 from __future__ import annotations
 
@@ -123,3 +126,36 @@ def error_norms(got: np.ndarray, ref: np.ndarray):
     rel_l2 = float(np.sqrt(np.dot(d, d)) / nref) if nref > 0 else float(np.sqrt(np.dot(d, d)))
     rel_max = float(np.max(np.abs(d)) / mref) if mref > 0 else float(np.max(np.abs(d), initial=0.0))
     return rel_l2, rel_max
+
+
+def min_line_cover(mask):
+    """Minimal axis-parallel line cover of a 2D weight pattern (Sec. 3.5).
+
+    ``mask`` is an n x n array whose nonzero entries mark the weights present.
+    A cover is a set of row lines and column lines such that every nonzero
+    (i, j) lies on row i or on column j of the set.  Brute force over every
+    set of row lines: once the rows are fixed, the columns that must be added
+    are exactly those holding a nonzero in a row left out.  Returns
+    (number of lines, rows, cols) for one minimal cover, rows and cols as
+    boolean arrays; among minimal covers the first one met is returned (row
+    sets in increasing binary order).  Exponential in n: small n only.
+    """
+    m = np.asarray(mask) != 0
+    n = m.shape[0]
+    if m.ndim != 2 or m.shape[1] != n:
+        raise ValueError("mask must be square")
+    if n > 16:
+        raise ValueError("brute force is for n <= 16")
+    best = None
+    for bits in range(1 << n):
+        rows = np.array([(bits >> i) & 1 for i in range(n)], dtype=bool)
+        cols = np.zeros(n, dtype=bool)
+        for i in range(n):
+            if not rows[i]:
+                for j in range(n):
+                    if m[i, j]:
+                        cols[j] = True
+        count = int(rows.sum() + cols.sum())
+        if best is None or count < best[0]:
+            best = (count, rows, cols)
+    return best

@@ -293,3 +293,51 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     lib.oracle_gather(2, shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 2, dp(c), 1,
                       ctypes.c_int64(2), dp(a), dp(out))
     assert not np.array_equal(out, fm.scatter(a, 2, c, "periodic", 2))
+
+
+# ---------------------------------------------------------------- minimal line cover (Sec. 3.5)
+def _covers(mask, rows, cols):
+    m = np.asarray(mask) != 0
+    return all(rows[i] or cols[j] for i, j in zip(*np.nonzero(m)))
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_min_line_cover_box_and_star(r):
+    """Table cls-2d: a box needs all 2r+1 lines; a star two (its row and column)."""
+    n = 2 * r + 1
+    count, rows, cols = oracle.min_line_cover(np.ones((n, n)))
+    assert count == n and _covers(np.ones((n, n)), rows, cols)
+    star = np.zeros((n, n))
+    star[r, :] = 1
+    star[:, r] = 1
+    count, rows, cols = oracle.min_line_cover(star)
+    assert count == 2 and rows[r] and cols[r] and rows.sum() == 1 and cols.sum() == 1
+
+
+def test_min_line_cover_special_cases():
+    assert oracle.min_line_cover(np.zeros((5, 5)))[0] == 0
+    one = np.zeros((5, 5))
+    one[3, 1] = 1
+    assert oracle.min_line_cover(one)[0] == 1
+    # no two weights share a line: one line per weight
+    perm = np.eye(7)[[3, 0, 6, 2, 5, 1, 4]]
+    assert oracle.min_line_cover(perm)[0] == 7
+    # a full row plus one weight elsewhere: the row and one more line
+    m = np.zeros((5, 5))
+    m[2, :] = 1
+    m[4, 0] = 1
+    assert oracle.min_line_cover(m)[0] == 2
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("density", [0.2, 0.5, 0.8])
+def test_min_line_cover_konig(n, density):
+    """Konig's theorem: the minimum line cover has as many lines as the largest
+    set of weights with no two in one row or column (brute force over
+    permutations), and the returned lines cover every weight."""
+    for seed in range(6):
+        mask = si.uniform(1000 * n + seed + int(100 * density), n * n).reshape(n, n) < density
+        count, rows, cols = oracle.min_line_cover(mask)
+        assert _covers(mask, rows, cols) and count == rows.sum() + cols.sum()
+        matching = max(sum(bool(mask[i, p[i]]) for i in range(n)) for p in itertools.permutations(range(n)))
+        assert count == matching
