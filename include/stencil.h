@@ -373,6 +373,23 @@ STENCIL_API stencil_status stencil_band_operand(int radius, const double *line, 
 STENCIL_API stencil_status stencil_line_cover(int ndim, int radius, stencil_kind kind, int option, int n,
                                   int32_t *n_lines, int64_t *outer_products);
 
+/* stencil_min_line_cover -- a minimal set of axis-parallel coefficient lines
+ * covering every weight of a 2D stencil of any pattern (Sec. 3.5: the rows
+ * and columns of the weight matrix form a bipartite graph whose edges are the
+ * weights, and a minimum vertex cover of it, found through a maximum matching
+ * and Konig's theorem, is a minimal line cover).
+ *   n        side of the weight matrix (2r+1), 1..64.
+ *   mask     n x n bytes, row-major; nonzero = a weight is present.
+ *   rows     [out] n entries: 1 if row line i (weights C[i][*]) is in the cover.
+ *   cols     [out] n entries: 1 if column line j (weights C[*][j]) is in the cover.
+ *   n_lines  [out] lines in the cover (sum of rows and cols).
+ * Host only; the caller owns every array.  Errors: EINVAL (NULL, n out of
+ * range).  The matrixized kernels run star and box patterns only; this is
+ * the plan algebra for others.
+ */
+STENCIL_API stencil_status stencil_min_line_cover(int n, const uint8_t *mask, int32_t *rows, int32_t *cols,
+                                                  int32_t *n_lines);
+
 /* Library version string. */
 STENCIL_API const char *stencil_version(void);
 

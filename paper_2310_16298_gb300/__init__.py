@@ -120,6 +120,7 @@ _SIGS = {
                                             ctypes.c_double, ctypes.c_double, _P]),
     "stencil_error_norms": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _DP, _P]),
     "stencil_band_operand": (ctypes.c_int, [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, _DP]),
+    "stencil_min_line_cover": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "stencil_line_cover": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _I64P]),
     "stencil_version": (ctypes.c_char_p, []),
@@ -373,6 +374,21 @@ def stencil_line_cover(ndim: int, radius: int, kind, option: int, n: int):
     _check(lib().stencil_line_cover(ndim, radius, k, option, n, ctypes.byref(nl), ctypes.byref(ops)),
            "stencil_line_cover")
     return nl.value, ops.value
+
+
+def stencil_min_line_cover(mask):
+    """(number of lines, rows, cols) of a minimal axis-parallel line cover of
+    the n x n weight pattern ``mask`` (nonzero = weight present)."""
+    m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+    if m.ndim != 2 or m.shape[0] != m.shape[1]:
+        raise ValueError("mask must be square")
+    n = m.shape[0]
+    rows = np.zeros(n, dtype=np.int32)
+    cols = np.zeros(n, dtype=np.int32)
+    count = ctypes.c_int32()
+    _check(lib().stencil_min_line_cover(n, m.ctypes.data, rows.ctypes.data, cols.ctypes.data, ctypes.byref(count)),
+           "stencil_min_line_cover")
+    return count.value, rows.astype(bool), cols.astype(bool)
 
 
 # ---------------------------------------------------------------- torch helper

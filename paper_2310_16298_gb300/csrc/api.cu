@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <memory>
@@ -493,6 +494,73 @@ extern "C" stencil_status stencil_line_cover(int ndim, int radius, stencil_kind 
     for (const auto& l : lines) ops += line_outer_products(l, n);
     *n_lines = (int32_t)lines.size();
     *outer_products = ops;
+    return STENCIL_OK;
+}
+
+// Minimal axis-parallel line cover of a 2D weight pattern (Sec. 3.5): the
+// rows and the columns of the weight matrix are the two vertex sets of a
+// bipartite graph and every weight is an edge, so a minimal set of lines is a
+// minimum vertex cover.  A maximum matching is grown by augmenting paths; by
+// Konig's theorem the rows that the alternating paths from the unmatched rows
+// do not reach, together with the columns they do reach, form a vertex cover
+// with as many vertices as the matching has edges, hence a minimum one.
+namespace {
+constexpr int kMaxCoverSide = 64;
+
+bool augment(int u, int n, const uint8_t* mask, std::vector<int>& row_of_col, std::vector<int>& col_of_row,
+             std::vector<char>& seen) {
+    for (int v = 0; v < n; ++v) {
+        if (!mask[(size_t)u * n + v] || seen[v]) continue;
+        seen[v] = 1;
+        if (row_of_col[v] < 0 || augment(row_of_col[v], n, mask, row_of_col, col_of_row, seen)) {
+            row_of_col[v] = u;
+            col_of_row[u] = v;
+            return true;
+        }
+    }
+    return false;
+}
+}  // namespace
+
+extern "C" stencil_status stencil_min_line_cover(int n, const uint8_t* mask, int32_t* rows, int32_t* cols,
+                                                 int32_t* n_lines) {
+    if (!mask || !rows || !cols || !n_lines) return fail(STENCIL_EINVAL, "NULL argument");
+    if (n < 1 || n > kMaxCoverSide) return fail(STENCIL_EINVAL, "n must be in 1..64");
+    std::vector<int> row_of_col(n, -1), col_of_row(n, -1);
+    std::vector<char> seen(n);
+    for (int u = 0; u < n; ++u) {
+        std::fill(seen.begin(), seen.end(), 0);
+        augment(u, n, mask, row_of_col, col_of_row, seen);
+    }
+    // Alternating paths from the unmatched rows: row -> column along any
+    // weight, column -> row along its matching edge.
+    std::vector<char> zr(n, 0), zc(n, 0);
+    std::vector<int> todo;
+    for (int u = 0; u < n; ++u)
+        if (col_of_row[u] < 0) {
+            zr[u] = 1;
+            todo.push_back(u);
+        }
+    while (!todo.empty()) {
+        const int u = todo.back();
+        todo.pop_back();
+        for (int v = 0; v < n; ++v) {
+            if (!mask[(size_t)u * n + v] || zc[v]) continue;
+            zc[v] = 1;
+            const int w = row_of_col[v];
+            if (w >= 0 && !zr[w]) {
+                zr[w] = 1;
+                todo.push_back(w);
+            }
+        }
+    }
+    int32_t count = 0;
+    for (int i = 0; i < n; ++i) {
+        rows[i] = zr[i] ? 0 : 1;
+        cols[i] = zc[i] ? 1 : 0;
+        count += rows[i] + cols[i];
+    }
+    *n_lines = count;
     return STENCIL_OK;
 }
 

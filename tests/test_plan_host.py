@@ -6,7 +6,9 @@ import re
 import numpy as np
 import pytest
 
+import oracle
 import paper_2310_16298_gb300 as sx
+import stencil_inputs as si
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GOLDEN = os.path.join(ROOT, "tests", "golden")
@@ -121,3 +123,47 @@ def test_batch_create_rejects_out_of_range_depth_and_shape(tb, tile_shape):
 def test_unknown_ticket_is_rejected():
     assert sx.stencil_poll(123456789) == sx.EINVAL
     assert sx.stencil_wait(123456789, 0) == sx.EINVAL
+
+
+# ---------------------------------------------------------------- minimal line cover (Sec. 3.5)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 9])
+@pytest.mark.parametrize("density", [0.15, 0.4, 0.7, 1.0])
+def test_min_line_cover_matches_oracle(n, density):
+    for seed in range(8):
+        mask = si.uniform(7919 * n + seed + int(1000 * density), n * n).reshape(n, n) < density
+        count, rows, cols = sx.stencil_min_line_cover(mask)
+        want = oracle.min_line_cover(mask)[0]
+        assert count == want == rows.sum() + cols.sum()
+        assert all(rows[i] or cols[j] for i, j in zip(*np.nonzero(mask)))
+
+
+def test_min_line_cover_star_and_box_agree_with_line_cover_counts():
+    for r in (1, 2, 3, 4):
+        n = 2 * r + 1
+        star = np.zeros((n, n), dtype=bool)
+        star[r, :] = star[:, r] = True
+        assert sx.stencil_min_line_cover(star)[0] == sx.stencil_line_cover(2, r, "star", 1, 8)[0] == 2
+        assert sx.stencil_min_line_cover(np.ones((n, n)))[0] == sx.stencil_line_cover(2, r, "box", 0, 8)[0] == n
+
+
+@pytest.mark.parametrize("n", [16, 33, 64])
+def test_min_line_cover_large_konig(n):
+    """Large patterns: a valid cover whose size equals a maximum matching
+    (Konig's theorem), the matching taken from SciPy."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    import scipy.sparse as sp
+    for seed in range(4):
+        mask = si.uniform(31 * n + seed, n * n).reshape(n, n) < 0.08
+        count, rows, cols = sx.stencil_min_line_cover(mask)
+        assert all(rows[i] or cols[j] for i, j in zip(*np.nonzero(mask)))
+        match = csgraph.maximum_bipartite_matching(sp.csr_matrix(mask.astype(np.int8)), perm_type="column")
+        assert count == int((match >= 0).sum())
+
+
+def test_min_line_cover_rejects_bad_sizes():
+    with pytest.raises(sx.StencilError):
+        sx.stencil_min_line_cover(np.zeros((0, 0)))
+    with pytest.raises(sx.StencilError):
+        sx.stencil_min_line_cover(np.ones((65, 65)))
