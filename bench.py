@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
     ap.add_argument("--dtype", default="", choices=["", "f32", "f64"], help="storage type ('' = the workload's own)")
-    ap.add_argument("--prec", default="native", choices=["native", "tf32", "tf32x3", "bf16", "bf16x2", "bf16x3"],
+    ap.add_argument("--prec", default="native", choices=["native", "tf32", "tf32x3", "bf16", "bf16x2", "bf16x3", "bf16w2"],
                     help="matrixized arithmetic (native = TF32x3 for FP32)")
     ap.add_argument("--cover", default="auto", choices=["auto", "parallel", "hybrid"],
                     help="line cover of star stencils on the matrixized kernel")
@@ -218,12 +218,43 @@ def oracle_baseline(p, field, max_seconds=20.0):
                       f"{dt:.1f} s, FP64 gather definition, OpenMP over rows"}
 
 
-def sample_points(shape, n=8, seed=77):
+# Tile periods of the matrixized kernels along each axis (slowest first):
+# 2D tiles are 4 lane quarters of 2 (32 - 2 ceil(r/2)) rows by 2 items of 16
+# columns; 3D work units are 32-plane chunks by 4 quarters of 32 - 2r rows by
+# 16 or 32 columns.  Seams between them are sampled on purpose.
+def tile_periods(ndim, r):
+    if ndim == 2:
+        q = 2 * (32 - 2 * ((r + 1) // 2))
+        return [(q, 4 * q), (16, 32)]
+    q = 32 - 2 * r
+    return [(32,), (q, 4 * q), (16, 32)]
+
+
+def sample_points(shape, r, n=64, n_random=8, seed=77):
+    """Output points checked against the oracle: every corner (the periodic
+    wrap in every axis), then points whose coordinates sit on either side of
+    tile, quarter and item seams, near both edges and mid-grid, then a few
+    uniform random points."""
     rng = np.random.default_rng(seed)
-    pts = np.stack([rng.integers(0, s, size=n) for s in shape], axis=1)
-    pts[0] = 0
-    pts[1] = np.array(shape) - 1
-    return pts
+    ndim = len(shape)
+    cands = []
+    for ax, (nax, periods) in enumerate(zip(shape, tile_periods(ndim, r))):
+        c = {0, 1, 2, nax // 2, nax - 3, nax - 2, nax - 1}
+        for P in periods:
+            for k in (1, 2, max(1, nax // P // 2), nax // P):
+                c.update((k * P - 1, k * P))
+        cands.append(sorted(v for v in c if 0 <= v < nax))
+    pts = [list(p) for p in np.ndindex(*([2] * ndim))]
+    pts = [[0 if b == 0 else shape[d] - 1 for d, b in enumerate(p)] for p in pts]
+    seen = {tuple(p) for p in pts}
+    while len(pts) < n:
+        p = tuple(int(rng.choice(c)) for c in cands)
+        if p not in seen:
+            seen.add(p)
+            pts.append(list(p))
+    for _ in range(n_random):
+        pts.append([int(rng.integers(0, s)) for s in shape])
+    return np.array(pts, dtype=np.int64)
 
 
 def sine_closed_form(p, field, pts):
@@ -323,7 +354,7 @@ def run_batch_workload(args):
     if rank == 0:
         for i in (0, len(probs) // 2, len(probs) - 1):
             p = probs[i]
-            pts = sample_points(p.shape, n=4, seed=i)
+            pts = sample_points(p.shape, p.r, n=8, n_random=2, seed=i)
             want = oracle.sample(p.field(), p.r, p.coeffs, p.bc, p.steps, pts)
             got = ys[i][tuple(torch.as_tensor(c, device=dev) for c in pts.T)].double().cpu().numpy()
             errs.append(oracle.error_norms(got, want))
@@ -370,7 +401,7 @@ def run_error_growth(args):
     x = torch.tensor(field, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
     modes = [("gather", "native"), ("matrixized", "tf32x3"), ("matrixized", "bf16x3"), ("matrixized", "bf16x2"),
-             ("matrixized", "tf32"), ("matrixized", "bf16")]
+             ("matrixized", "tf32"), ("matrixized", "bf16"), ("matrixized", "bf16w2")]
     table = {}
     for steps in (10, 100, 1000):
         ref = oracle.gather(field, p.r, p.coeffs, p.bc, steps)
@@ -520,7 +551,7 @@ def main():
 
     # accuracy of each implementation at sampled points (oracle on the dependency cone)
     import oracle
-    pts = sample_points(p.shape)
+    pts = sample_points(p.shape, p.r)
     if p.field_kind == "sine":
         # long runs: every point depends on the whole grid, so the check is
         # the closed form (the field is an eigenvector of the symmetric stencil)

@@ -65,14 +65,19 @@ typedef enum { STENCIL_BC_DIRICHLET_ZERO = 0, STENCIL_BC_PERIODIC = 1 } stencil_
  * storage type on CUDA cores (FP32 FMA or FP64 DFMA).  TF32 / BF16 run the
  * outer products on the tensor cores with FP32 accumulation; the X2/X3 forms
  * split each operand into 2 or 3 parts (hi + lo [+ lo2]) and keep the partial
- * products listed in the design notes, which restores FP32-level accuracy. */
+ * products listed in the design notes, which restores FP32-level accuracy.
+ * BF16_W2 rounds the field to one BF16 part but keeps the weights as two BF16
+ * parts (two products per MMA step): plain-BF16 inputs without the amplitude
+ * drift that BF16-rounded weights cause over many steps (their sum is off by
+ * up to 2^-9, an error that grows linearly with the step count). */
 typedef enum {
     STENCIL_PREC_NATIVE = 0,
     STENCIL_PREC_TF32 = 1,
     STENCIL_PREC_TF32X3 = 2,
     STENCIL_PREC_BF16 = 3,
     STENCIL_PREC_BF16X2 = 4,
-    STENCIL_PREC_BF16X3 = 5
+    STENCIL_PREC_BF16X3 = 5,
+    STENCIL_PREC_BF16_W2 = 6
 } stencil_precision;
 
 typedef enum {
@@ -112,7 +117,8 @@ typedef struct {
     int32_t n_scalar;     /* coefficients applied on CUDA cores beside the lines        */
     int32_t tile_n;       /* output columns per outer-product block (0 for GATHER)      */
     int64_t scratch_bytes;/* device scratch owned by the plan                           */
-    int32_t device_error; /* nonzero once a kernel of the plan gave up a bounded wait     */
+    int32_t device_error; /* error bits: nonzero once a kernel of the plan gave up a
+                             bounded wait (or stencil_plan_raise_error set bits)        */
     int32_t reserved;
 } stencil_plan_info_t;
 
@@ -150,6 +156,22 @@ STENCIL_API stencil_status stencil_plan_destroy(stencil_plan_t plan);
 /* Describe the plan (host only, no GPU work). */
 STENCIL_API stencil_status stencil_plan_info(stencil_plan_t plan, stencil_plan_info_t *info);
 
+/* Device errors.  Every wait inside the matrixized kernels is bounded; a
+ * kernel that runs one out sets error bits in a host-mapped word of its plan,
+ * drains its copies in flight, frees its tensor memory and returns, so the
+ * CUDA context stays usable but the output of that sweep is not valid.  The
+ * bits are sticky until the plan is destroyed, and every call that runs or
+ * completes work of the plan reports them as STENCIL_ECUDA with a message:
+ * stencil_apply, stencil_apply_noalloc, stencil_apply_host and
+ * stencil_submit (before queueing), stencil_poll and stencil_wait (once the
+ * work has finished), stencil_batch_launch (any plan of the batch),
+ * stencil_batch_run (after the run), and the server's request status.
+ *
+ * stencil_plan_raise_error -- set error bits of a plan from the host, as a
+ * kernel that gave up a wait would: host-side fault injection, used to test
+ * the error paths without making a GPU fault.  bits != 0.  Errors: EINVAL. */
+STENCIL_API stencil_status stencil_plan_raise_error(stencil_plan_t plan, uint32_t bits);
+
 /* ---------------------------------------------------------------------------
  * Sweeps.
  *
@@ -160,7 +182,8 @@ STENCIL_API stencil_status stencil_plan_info(stencil_plan_t plan, stencil_plan_i
  *   d_in    device array, dtype of the plan, read only (unless == d_out).
  *   d_out   device array of the same size; may equal d_in.
  *   steps   >= 0; 0 copies d_in to d_out.
- * Errors: EINVAL (NULL pointer, steps < 0), ECUDA (launch failure).
+ * Errors: EINVAL (NULL pointer, steps < 0), ECUDA (launch failure, or the
+ * plan's error bits are set: see stencil_plan_raise_error).
  * Concurrent applies of one plan must be ordered by the caller: they share
  * the plan's scratch grid and, for the matrixized kernels, the plan's
  * device tile counter (tiles are handed out to the SMs at run time; the
@@ -173,7 +196,7 @@ STENCIL_API stencil_status stencil_apply(stencil_plan_t plan, const void *d_in, 
  * device memory while they run steps (code inside another runtime's stream
  * work, processes whose device memory is budgeted up front, real-time loops
  * that cannot take cudaMalloc's synchronisation).  The paper has no
- * counterpart: this is a deployment variant of the time loop of Sec. 2.2.
+ * counterpart.
  *
  * Same arguments, layout and result as stencil_apply, but the second grid copy
  * of the ping-pong is a file-scope device array of 16 MiB (4 Mi FP32 or 2 Mi
@@ -195,7 +218,10 @@ STENCIL_API stencil_status stencil_apply_noalloc(stencil_plan_t plan, const void
 
 /* Host-to-host convenience: copy h_in to the device, apply, copy the result
  * to h_out (both host arrays of the plan's dtype, pinned or pageable), and
- * synchronise.  Uses two device grids allocated per call. */
+ * synchronise.  The field is advanced in place in a device staging grid that
+ * the plan allocates on its first stencil_apply_host call and keeps until it
+ * is destroyed (so later calls allocate nothing); the copies and sweeps run
+ * on the plan's own stream.  Errors: EINVAL, ENOMEM (staging grid), ECUDA. */
 STENCIL_API stencil_status stencil_apply_host(stencil_plan_t plan, const void *h_in, void *h_out, int64_t steps);
 
 /* ---------------------------------------------------------------------------
@@ -272,8 +298,9 @@ STENCIL_API stencil_status stencil_batch_run(int n, const stencil_plan_t *plans,
  * Serving: continuous batching of stencil solves.
  *
  * A server owns a worker thread.  Submitted requests are admitted in arrival
- * order while the device-memory budget (each request is charged three grids
- * plus 1 MiB: two copies and its plan's scratch grid) and the resident-slot
+ * order while the device-memory budget (each request is charged two grids
+ * plus 1 MiB: its own grid, advanced in place, and its plan's scratch grid,
+ * the second copy of the ping-pong) and the resident-slot
  * limit allow.  Every resident request advances by at most `quantum_steps`
  * time steps per issue on one of `nstreams` streams, so requests overlap on
  * the device and new ones join as soon as memory and a slot free up.  A

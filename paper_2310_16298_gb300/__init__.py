@@ -27,14 +27,14 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EBUSY", "ENOTREADY", "ETIMED
 STAR, BOX = 0, 1
 F32, F64 = 0, 1
 BC_DIRICHLET_ZERO, BC_PERIODIC = 0, 1
-PREC_NATIVE, PREC_TF32, PREC_TF32X3, PREC_BF16, PREC_BF16X2, PREC_BF16X3 = range(6)
+PREC_NATIVE, PREC_TF32, PREC_TF32X3, PREC_BF16, PREC_BF16X2, PREC_BF16X3, PREC_BF16_W2 = range(7)
 IMPL_AUTO, IMPL_GATHER, IMPL_MATRIXIZED = range(3)
 
 KINDS = {"star": STAR, "box": BOX}
 DTYPES = {"f32": F32, "f64": F64}
 BCS = {"dirichlet": BC_DIRICHLET_ZERO, "periodic": BC_PERIODIC}
 PRECS = {"native": PREC_NATIVE, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3, "bf16": PREC_BF16,
-         "bf16x2": PREC_BF16X2, "bf16x3": PREC_BF16X3}
+         "bf16x2": PREC_BF16X2, "bf16x3": PREC_BF16X3, "bf16w2": PREC_BF16_W2}
 IMPLS = {"auto": IMPL_AUTO, "gather": IMPL_GATHER, "matrixized": IMPL_MATRIXIZED}
 
 
@@ -91,6 +91,7 @@ _SIGS = {
                                            ctypes.POINTER(stencil_options)]),
     "stencil_plan_destroy": (ctypes.c_int, [_P]),
     "stencil_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(stencil_plan_info_t)]),
+    "stencil_plan_raise_error": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "stencil_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
     "stencil_apply_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
     "stencil_apply_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
@@ -204,6 +205,10 @@ def stencil_plan_info(plan: int) -> dict:
     info = stencil_plan_info_t()
     _check(lib().stencil_plan_info(plan, ctypes.byref(info)), "stencil_plan_info")
     return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def stencil_plan_raise_error(plan: int, bits: int):
+    _check(lib().stencil_plan_raise_error(plan, int(bits)), "stencil_plan_raise_error")
 
 
 def stencil_apply(plan: int, d_in: int, d_out: int, steps: int, stream: int = 0):

@@ -89,21 +89,67 @@ stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out,
     return STENCIL_OK;
 }
 
+unsigned int plan_error_bits(const stencil_plan_s* p) {
+    unsigned int w = *(volatile const unsigned int*)&p->host_error;
+    if (p->mx) w |= mx_device_error(*p->mx);
+    return w;
+}
+
+stencil_status plan_error_status(const stencil_plan_s* p, const char* where) {
+    const unsigned int w = plan_error_bits(p);
+    if (!w) return STENCIL_OK;
+    char buf[64];
+    snprintf(buf, sizeof(buf), "0x%x", w);
+    return fail(STENCIL_ECUDA, std::string(where) + ": a kernel of this plan gave up a bounded wait (error bits " +
+                                   buf + "); the plan's results since then are not valid: destroy the plan");
+}
+
 }  // namespace stx
 
 namespace {
 
+// ----------------------------------------------------------------- live plans
+// Tickets name their plan by id, so a poll after the plan was destroyed finds
+// no plan instead of a dangling pointer.
+std::mutex g_plans_mu;
+std::unordered_map<uint64_t, stencil_plan_s*> g_plans;
+uint64_t g_next_plan_id = 1;
+
+void plan_register(stencil_plan_s* p) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    p->id = g_next_plan_id++;
+    g_plans[p->id] = p;
+}
+
+void plan_unregister(stencil_plan_s* p) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plans.erase(p->id);
+}
+
+// Error status of the plan with this id once its work has completed (OK when
+// the plan no longer exists).
+stencil_status plan_error_status_by_id(uint64_t id, const char* where) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    auto it = g_plans.find(id);
+    if (it == g_plans.end()) return STENCIL_OK;
+    return plan_error_status(it->second, where);
+}
+
 // ----------------------------------------------------------------- tickets
+struct Ticket {
+    cudaEvent_t ev;
+    uint64_t plan_id;
+};
 std::mutex g_tk_mu;
-std::unordered_map<uint64_t, cudaEvent_t> g_tickets;
+std::unordered_map<uint64_t, Ticket> g_tickets;
 std::vector<cudaEvent_t> g_event_pool;
 uint64_t g_next_ticket = 1;
 
-stencil_status ticket_status(uint64_t ticket, cudaEvent_t* ev) {
+stencil_status ticket_status(uint64_t ticket, Ticket* t) {
     std::lock_guard<std::mutex> lk(g_tk_mu);
     auto it = g_tickets.find(ticket);
     if (it == g_tickets.end()) return fail(STENCIL_EINVAL, "unknown or already released ticket");
-    *ev = it->second;
+    *t = it->second;
     return STENCIL_OK;
 }
 
@@ -111,9 +157,16 @@ void ticket_release(uint64_t ticket) {
     std::lock_guard<std::mutex> lk(g_tk_mu);
     auto it = g_tickets.find(ticket);
     if (it != g_tickets.end()) {
-        g_event_pool.push_back(it->second);
+        g_event_pool.push_back(it->second.ev);
         g_tickets.erase(it);
     }
+}
+
+// Status of a ticket whose event has completed with `e`.
+stencil_status ticket_done(uint64_t ticket, const Ticket& t, cudaError_t e) {
+    ticket_release(ticket);
+    if (e != cudaSuccess) return cuda_fail(e, "submitted work");
+    return plan_error_status_by_id(t.plan_id, "submitted work");
 }
 
 }  // namespace
@@ -162,7 +215,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     }
     const bool f64 = (dtype == STENCIL_F64);
     const int prec = o.prec;
-    if (prec < STENCIL_PREC_NATIVE || prec > STENCIL_PREC_BF16X3) return fail(STENCIL_EINVAL, "prec out of range");
+    if (prec < STENCIL_PREC_NATIVE || prec > STENCIL_PREC_BF16_W2) return fail(STENCIL_EINVAL, "prec out of range");
     if (f64 && prec != STENCIL_PREC_NATIVE) return fail(STENCIL_EINVAL, "TF32/BF16 precisions need F32 storage");
     if (o.impl == STENCIL_IMPL_GATHER && prec != STENCIL_PREC_NATIVE)
         return fail(STENCIL_EINVAL, "the gather kernel computes in the storage type (prec NATIVE)");
@@ -244,14 +297,17 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
         }
         return cuda_fail(e, "cudaStreamCreate");
     }
+    plan_register(p.get());
     *out = p.release();
     return STENCIL_OK;
 }
 
 extern "C" stencil_status stencil_plan_destroy(stencil_plan_t p) {
     if (!p) return STENCIL_OK;
+    plan_unregister(p);
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->scratch) cudaFree(p->scratch);
+    if (p->staging) cudaFree(p->staging);
     if (p->stream) cudaStreamDestroy(p->stream);
     if (p->mx) {
         mx_plan_free(p->mx);
@@ -272,8 +328,15 @@ extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_
         info->n_lines = p->mx->n_lines;
         info->n_scalar = p->mx->n_scalar;
         info->tile_n = p->mx->nb;
-        info->device_error = (int32_t)mx_device_error(*p->mx);
     }
+    info->device_error = (int32_t)plan_error_bits(p);
+    return STENCIL_OK;
+}
+
+extern "C" stencil_status stencil_plan_raise_error(stencil_plan_t p, uint32_t bits) {
+    if (!p) return fail(STENCIL_EINVAL, "NULL plan");
+    if (!bits) return fail(STENCIL_EINVAL, "bits must be nonzero");
+    __atomic_fetch_or(&p->host_error, bits, __ATOMIC_SEQ_CST);
     return STENCIL_OK;
 }
 
@@ -282,32 +345,38 @@ extern "C" stencil_status stencil_apply(stencil_plan_t p, const void* d_in, void
                                         stencil_stream_t stream) {
     if (!p || !d_in || !d_out) return fail(STENCIL_EINVAL, "NULL argument");
     if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    stencil_status st = plan_error_status(p, "stencil_apply");
+    if (st != STENCIL_OK) return st;
     return time_loop(p, d_in, d_out, steps, (cudaStream_t)stream, p->scratch);
 }
 
+// The field goes to the plan's staging grid, is advanced there in place (the
+// time loop ping-pongs through the plan's scratch grid) and comes back: one
+// device grid beyond the plan's own, allocated by the first call.
 extern "C" stencil_status stencil_apply_host(stencil_plan_t p, const void* h_in, void* h_out, int64_t steps) {
     if (!p || !h_in || !h_out) return fail(STENCIL_EINVAL, "NULL argument");
     if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
-    void *a = nullptr, *b = nullptr;
-    cudaError_t e = cudaMalloc(&a, p->grid_bytes);
-    if (e != cudaSuccess) return fail(STENCIL_ENOMEM, "device grid");
-    e = cudaMalloc(&b, p->grid_bytes);
-    if (e != cudaSuccess) {
-        cudaFree(a);
-        return fail(STENCIL_ENOMEM, "device grid");
+    stencil_status st = plan_error_status(p, "stencil_apply_host");
+    if (st != STENCIL_OK) return st;
+    cudaError_t e;
+    if (!p->staging) {
+        e = cudaMalloc(&p->staging, p->grid_bytes);
+        if (e != cudaSuccess) {
+            p->staging = nullptr;
+            cudaGetLastError();
+            return fail(STENCIL_ENOMEM, std::string("staging grid: ") + cudaGetErrorString(e));
+        }
     }
-    stencil_status st = STENCIL_OK;
-    e = cudaMemcpyAsync(a, h_in, p->grid_bytes, cudaMemcpyHostToDevice, p->stream);
+    e = cudaMemcpyAsync(p->staging, h_in, p->grid_bytes, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "H2D copy");
-    if (st == STENCIL_OK) st = time_loop(p, a, b, steps, p->stream, p->scratch);
+    if (st == STENCIL_OK) st = time_loop(p, p->staging, p->staging, steps, p->stream, p->scratch);
     if (st == STENCIL_OK) {
-        e = cudaMemcpyAsync(h_out, b, p->grid_bytes, cudaMemcpyDeviceToHost, p->stream);
+        e = cudaMemcpyAsync(h_out, p->staging, p->grid_bytes, cudaMemcpyDeviceToHost, p->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "D2H copy");
     }
     e = cudaStreamSynchronize(p->stream);
     if (st == STENCIL_OK && e != cudaSuccess) st = cuda_fail(e, "stencil_apply_host");
-    cudaFree(a);
-    cudaFree(b);
+    if (st == STENCIL_OK) st = plan_error_status(p, "stencil_apply_host");
     return st;
 }
 
@@ -357,8 +426,10 @@ extern "C" stencil_status stencil_apply_noalloc(stencil_plan_t p, const void* d_
     if (p->grid_bytes > kNoAllocScratchBytes)
         return fail(STENCIL_EINVAL, "grid of " + std::to_string(p->grid_bytes) +
                                         " bytes exceeds the 16 MiB static scratch of stencil_apply_noalloc");
+    stencil_status st = plan_error_status(p, "stencil_apply_noalloc");
+    if (st != STENCIL_OK) return st;
     void* scratch = nullptr;
-    stencil_status st = noalloc_scratch(&scratch);
+    st = noalloc_scratch(&scratch);
     if (st != STENCIL_OK) return st;
     return time_loop(p, d_in, d_out, steps, (cudaStream_t)stream, scratch);
 }
@@ -368,7 +439,9 @@ extern "C" stencil_status stencil_submit(stencil_plan_t p, const void* d_in, voi
                                          uint64_t* ticket) {
     if (!p || !d_in || !d_out || !ticket) return fail(STENCIL_EINVAL, "NULL argument");
     if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
-    stencil_status st = time_loop(p, d_in, d_out, steps, p->stream, p->scratch);
+    stencil_status st = plan_error_status(p, "stencil_submit");
+    if (st != STENCIL_OK) return st;
+    st = time_loop(p, d_in, d_out, steps, p->stream, p->scratch);
     if (st != STENCIL_OK) return st;
     cudaEvent_t ev = nullptr;
     {
@@ -385,33 +458,27 @@ extern "C" stencil_status stencil_submit(stencil_plan_t p, const void* d_in, voi
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     std::lock_guard<std::mutex> lk(g_tk_mu);
     *ticket = g_next_ticket++;
-    g_tickets[*ticket] = ev;
+    g_tickets[*ticket] = Ticket{ev, p->id};
     return STENCIL_OK;
 }
 
 extern "C" stencil_status stencil_poll(uint64_t ticket) {
-    cudaEvent_t ev;
-    stencil_status st = ticket_status(ticket, &ev);
+    Ticket t;
+    stencil_status st = ticket_status(ticket, &t);
     if (st != STENCIL_OK) return st;
-    cudaError_t e = cudaEventQuery(ev);
+    cudaError_t e = cudaEventQuery(t.ev);
     if (e == cudaErrorNotReady) return fail(STENCIL_ENOTREADY, "work not finished");
-    ticket_release(ticket);
-    if (e != cudaSuccess) return cuda_fail(e, "submitted work");
-    return STENCIL_OK;
+    return ticket_done(ticket, t, e);
 }
 
 extern "C" stencil_status stencil_wait(uint64_t ticket, int64_t timeout_ms) {
-    cudaEvent_t ev;
-    stencil_status st = ticket_status(ticket, &ev);
+    Ticket t;
+    stencil_status st = ticket_status(ticket, &t);
     if (st != STENCIL_OK) return st;
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        cudaError_t e = cudaEventQuery(ev);
-        if (e != cudaErrorNotReady) {
-            ticket_release(ticket);
-            if (e != cudaSuccess) return cuda_fail(e, "submitted work");
-            return STENCIL_OK;
-        }
+        cudaError_t e = cudaEventQuery(t.ev);
+        if (e != cudaErrorNotReady) return ticket_done(ticket, t, e);
         if (timeout_ms >= 0) {
             const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
                                  std::chrono::steady_clock::now() - t0).count();

@@ -28,6 +28,7 @@ struct stencil_batch_s {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<const stencil_plan_s*> plans;  // error bits are checked at every launch
 };
 
 namespace {
@@ -249,6 +250,7 @@ extern "C" stencil_status stencil_batch_create_ex(stencil_batch_t* out, int n, c
     std::unique_ptr<stencil_batch_s, void (*)(stencil_batch_s*)> b(new stencil_batch_s, batch_free);
     b->n = n;
     b->packed = packed;
+    b->plans.assign(plans, plans + n);
     for (int i = 0; i < n; ++i) b->updates += plans[i]->points * steps[i];
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
@@ -312,6 +314,10 @@ extern "C" stencil_status stencil_batch_create(stencil_batch_t* out, int n, cons
 
 extern "C" stencil_status stencil_batch_launch(stencil_batch_t b, stencil_stream_t stream) {
     if (!b) return fail(STENCIL_EINVAL, "NULL batch");
+    for (const stencil_plan_s* p : b->plans) {
+        stencil_status st = plan_error_status(p, "stencil_batch_launch");
+        if (st != STENCIL_OK) return st;
+    }
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return STENCIL_OK;
@@ -347,5 +353,6 @@ extern "C" stencil_status stencil_batch_run(int n, const stencil_plan_t* plans, 
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     stencil_batch_destroy(b);
     if (st == STENCIL_OK && e != cudaSuccess) st = cuda_fail(e, "batch run");
+    for (int i = 0; i < n && st == STENCIL_OK; ++i) st = plan_error_status(plans[i], "stencil_batch_run");
     return st;
 }

@@ -49,7 +49,9 @@
 // Two or three accumulator sets and A stages (as many as tensor memory
 // holds) overlap split, MMA and epilogue; every wait is bounded
 // (a timeout sets a host-visible error word, drains copies in flight and
-// frees tensor memory).
+// frees tensor memory).  Every CTA loads the banded operands from one of
+// several identical copies, so the CTAs starting together do not all read
+// the same L2 lines.
 //
 // Precision: TF32, TF32x3, BF16, BF16x2, BF16x3 (operand parts products
 // accumulated smallest first in FP32; the epilogue sums the blocks in FP32
@@ -85,6 +87,7 @@ constexpr int kSplitWarps = 2 * kQuarters;   // (quarter, input row parity)
 constexpr int kEpiWarps = 2 * kQuarters;     // (quarter, output row parity)
 constexpr int kMma2Warp = 2 + kSplitWarps + kEpiWarps;   // second MMA issuer
 constexpr int kThreads = 32 * (kMma2Warp + 1);
+constexpr int kBopCopies = 16;          // copies of the banded operands in global memory
 constexpr int kMaxRawStages = 6;
 constexpr int kTileRing = 8;            // tile ids handed from the producer to the epilogue
 constexpr int kTmemCols = 512;
@@ -259,7 +262,8 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             ptx::mbar_arrive_expect_tx(bop_bar, args.bop_bytes);
-            ptx::bulk_load(bops, args.bops, args.bop_bytes, bop_bar);
+            ptx::bulk_load(bops, (const unsigned char*)args.bops + (size_t)(blockIdx.x % kBopCopies) * args.bop_bytes,
+                           args.bop_bytes, bop_bar);
             for (int i = 0;; ++i) {
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
@@ -376,9 +380,7 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 }
                 ptx::tc_fence_after();
                 const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
-#pragma unroll
-                for (int g = 0; g < NG; ++g) split_store<BF, NP>(x[g], abase, PC, e * W + GW * g);
-                ptx::tmem_wait_st();
+                split_store_groups<BF, NP, NG>(x, abase, PC, e * W, GW);
                 ptx::tc_fence_before();
                 if (warp == 2 && lane == 0) a_tile[sa] = t;
                 __syncwarp();
@@ -421,22 +423,37 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 float acc[kNb];
 #pragma unroll
                 for (int b0 = 0; b0 < G::NBP; b0 += LB) {
+                    // Blocks b0 .. b0 + nv - 1 into v (and, with the first batch,
+                    // block I0 into v0 when it lies in a later batch), loaded and
+                    // waited for in one step.
                     uint32_t v[LB][kNb];
                     uint32_t v0[kNb];
-                    if (b0 == 0) ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)(I0 * kNb), v0);
-#pragma unroll
-                    for (int j = 0; j < LB; ++j)
-                        if (b0 + j < G::NBP && b0 + j != I0)
-                            ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((b0 + j) * kNb), v[j]);
-                    ptx::tmem_wait_ld();
+                    const int nv = G::NBP - b0 < LB ? G::NBP - b0 : LB;
+                    const uint32_t ba = dbase + (uint32_t)(b0 * kNb);
+                    const uint32_t bi = dbase + (uint32_t)(I0 * kNb);
+                    if (b0 == 0 && I0 >= LB) {
+                        if (nv == 2) ptx::tmem_ld_x16_sync(ba, v[0], ba + kNb, v[1], bi, v0);
+                        if (nv == 1) ptx::tmem_ld_x16_sync(ba, v[0], bi, v0);
+                    } else {
+                        if constexpr (LB >= 3) {
+                            if (nv == 3) ptx::tmem_ld_x16_sync(ba, v[0], ba + kNb, v[1], ba + 2 * kNb, v[2]);
+                        }
+                        if (nv == 2) ptx::tmem_ld_x16_sync(ba, v[0], ba + kNb, v[1]);
+                        if (nv == 1) ptx::tmem_ld_x16_sync(ba, v[0]);
+                    }
                     if (b0 + LB >= G::NBP) {   // last batch: the accumulator set is free
                         ptx::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) ptx::mbar_arrive(&acce[st]);
                     }
                     if (b0 == 0) {
+                        if constexpr (I0 < LB) {
 #pragma unroll
-                        for (int c = 0; c < kNb; ++c) acc[c] = __uint_as_float(v0[c]);
+                            for (int c = 0; c < kNb; ++c) acc[c] = __uint_as_float(v[I0][c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < kNb; ++c) acc[c] = __uint_as_float(v0[c]);
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < LB; ++j) {
@@ -602,8 +619,8 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "the hybrid line cover is built for 3D stars";
         return false;
     }
-    if (q.prec < STENCIL_PREC_TF32 || q.prec > STENCIL_PREC_BF16X3) {
-        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2 or BF16X3";
+    if (!mx_precision(q.prec)) {
+        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2, BF16X3 or BF16_W2";
         return false;
     }
     if (q.n[1] % 4 != 0) {
@@ -638,18 +655,21 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     std::vector<unsigned char> ops = pack_blocks(q.r, blocks, kNb, W, bf, &bpart);
     p->n_lines = 2 * q.r + 1;
     p->n_scalar = 0;
-    p->operand_bytes = ops.size();
+    const size_t one = ops.size();   // one copy; CTA b reads copy b % kBopCopies
+    p->operand_bytes = one * kBopCopies;
     const KernelInfo ki = kernel_for(q.r, bf, operand_parts(q.prec));
-    if (!ki.fn || ops.size() != (size_t)(bf ? 3 : 2) * bpart) {
+    if (!ki.fn || one != (size_t)(bf ? 3 : 2) * bpart || one % 16 != 0) {
         if (why) *why = "internal error: block operand size";
         return STENCIL_EUNSUPPORTED;
     }
+    std::vector<unsigned char> copies(p->operand_bytes);
+    for (int c = 0; c < kBopCopies; ++c) memcpy(copies.data() + c * one, ops.data(), one);
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {
         if (why) *why = std::string("operand upload: ") + cudaGetErrorString(e);
         return STENCIL_ENOMEM;
     }
-    e = cudaMemcpy(p->d_operands, ops.data(), p->operand_bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->d_operands, copies.data(), p->operand_bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(p->d_operands);
         p->d_operands = nullptr;
@@ -657,7 +677,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
         return STENCIL_ECUDA;
     }
     MxState* st = new MxState();
-    st->bop_bytes = (uint32_t)p->operand_bytes;
+    st->bop_bytes = (uint32_t)one;
     st->bpart_bytes = bpart;
     st->bf = bf;
     e = cudaHostAlloc((void**)&st->err_host, sizeof(unsigned int), cudaHostAllocMapped);

@@ -324,7 +324,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         }
                         split_store<BF>(x, abase, PC, c0, args.nparts);
                     }
-                    ptx::tmem_wait_st();
                     ptx::tc_fence_before();
                     if (warp == 2 && lane == 0) a_unit[sa] = 0;
                     __syncwarp();
@@ -364,14 +363,10 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         // input rows) x off-axis weights: z offsets without a row
                         // shift, y offsets shifted by b - R rows
                         uint32_t vx[CW], vi[CW];
-                        if constexpr (CW == 16) {
-                            ptx::tmem_ld_32x32b_x16(dbase, vx);
-                            ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)NB, vi);
-                        } else {
-                            ptx::tmem_ld_32x32b_x8(dbase, vx);
-                            ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)NB, vi);
-                        }
-                        ptx::tmem_wait_ld();
+                        if constexpr (CW == 16)
+                            ptx::tmem_ld_x16_sync(dbase, vx, dbase + (uint32_t)NB, vi);
+                        else
+                            ptx::tmem_ld_x8_sync(dbase, vx, dbase + (uint32_t)NB, vi);
 #pragma unroll
                         for (int c = 0; c < CW; ++c) acc[R][c] += __uint_as_float(vx[c]);
 #pragma unroll
@@ -399,17 +394,20 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     #pragma unroll
                         for (int l0 = 0; l0 < L; l0 += LB) {
                             uint32_t v[LB][CW];
-    #pragma unroll
-                            for (int j = 0; j < LB; ++j) {
-                                if (l0 + j < L) {
-                                    if constexpr (CW == 16) {
-                                        ptx::tmem_ld_32x32b_x16(dbase + (uint32_t)((l0 + j) * NB), v[j]);
-                                    } else {
-                                        ptx::tmem_ld_32x32b_x8(dbase + (uint32_t)((l0 + j) * NB), v[j]);
-                                    }
+                            const int nv = L - l0 < LB ? L - l0 : LB;   // lines in this batch
+                            const uint32_t ba = dbase + (uint32_t)(l0 * NB);
+                            if constexpr (CW == 16) {
+                                if (nv == 2) ptx::tmem_ld_x16_sync(ba, v[0], ba + NB, v[1]);
+                                if (nv == 1) ptx::tmem_ld_x16_sync(ba, v[0]);
+                            } else {
+                                if constexpr (LB >= 4) {
+                                    if (nv == 4)
+                                        ptx::tmem_ld_x8_sync(ba, v[0], ba + NB, v[1], ba + 2 * NB, v[2], ba + 3 * NB, v[3]);
+                                    if (nv == 3) ptx::tmem_ld_x8_sync(ba, v[0], ba + NB, v[1], ba + 2 * NB, v[2]);
                                 }
+                                if (nv == 2) ptx::tmem_ld_x8_sync(ba, v[0], ba + NB, v[1]);
+                                if (nv == 1) ptx::tmem_ld_x8_sync(ba, v[0]);
                             }
-                            ptx::tmem_wait_ld();
     #pragma unroll
                             for (int j = 0; j < LB; ++j) {
                                 const int l = l0 + j;
@@ -589,8 +587,8 @@ bool use_hybrid(const MxRequest& q) { return q.star && q.cover != STENCIL_COVER_
 }  // namespace
 
 bool mx3d_supported(const MxRequest& q, std::string* why) {
-    if (q.prec < STENCIL_PREC_TF32 || q.prec > STENCIL_PREC_BF16X3) {
-        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2 or BF16X3";
+    if (!mx_precision(q.prec)) {
+        if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2, BF16X3 or BF16_W2";
         return false;
     }
     if (q.bc != kBcDirichlet) {

@@ -71,9 +71,13 @@ inline int products_for(int prec) {
         case STENCIL_PREC_TF32X3: return 3;
         case STENCIL_PREC_BF16X2: return 3;
         case STENCIL_PREC_BF16X3: return 6;
+        case STENCIL_PREC_BF16_W2: return 2;
     }
     return 1;
 }
+
+// Precisions the outer-product kernels run.
+inline bool mx_precision(int prec) { return prec >= STENCIL_PREC_TF32 && prec <= STENCIL_PREC_BF16_W2; }
 
 inline int operand_parts(int prec) {
     switch (prec) {
@@ -85,48 +89,61 @@ inline int operand_parts(int prec) {
 }
 
 inline bool is_bf16(int prec) {
-    return prec == STENCIL_PREC_BF16 || prec == STENCIL_PREC_BF16X2 || prec == STENCIL_PREC_BF16X3;
+    return prec == STENCIL_PREC_BF16 || prec == STENCIL_PREC_BF16X2 || prec == STENCIL_PREC_BF16X3 ||
+           prec == STENCIL_PREC_BF16_W2;
 }
 
-// Issue every K step of one product (A part pa, B part pb) into accumulator
-// d; `first` clears the accumulator with the first step.
-template <bool BF, int KS>
+// Issue every K step of one product (A part PA, B part PB) into accumulator
+// d; FIRST clears the accumulator with the first step.
+template <bool BF, int KS, int PA, int PB, bool FIRST>
 __device__ __forceinline__ void issue_product(uint32_t d, uint32_t a_base, int part_cols, uint64_t b_desc0,
-                                              uint32_t bpart_bytes, int n, uint32_t idesc, int pa, int pb, bool first) {
-    const uint32_t a = a_base + (uint32_t)(pa * part_cols);
-    const uint64_t b = b_desc0 + (uint64_t)((pb * bpart_bytes) >> 4);
+                                              uint32_t bpart_bytes, int n, uint32_t idesc) {
+    const uint32_t a = a_base + (uint32_t)(PA * part_cols);
+    const uint64_t b = b_desc0 + (uint64_t)((PB * bpart_bytes) >> 4);
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
         const uint64_t bd = b + (uint64_t)((2 * ks * n * 16) >> 4);
-        const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-        if constexpr (BF) {
-            ptx::mma_f16_ts(d, a + 8 * ks, bd, idesc, acc);
-        } else {
-            ptx::mma_tf32_ts(d, a + 8 * ks, bd, idesc, acc);
-        }
+        if (FIRST && ks == 0)
+            ptx::mma_ts<BF, true>(d, a + 8 * ks, bd, idesc);
+        else
+            ptx::mma_ts<BF, false>(d, a + 8 * ks, bd, idesc);
     }
 }
 
 // Issue every product of one tile (A in tensor memory, B in shared memory)
-// into accumulator d, smallest products first: nprod = 1 (x0*h0), 3 (x1*h0,
-// x0*h1, x0*h0) or 6 (x0*h2, x1*h1, x2*h0, x1*h0, x0*h1, x0*h0).
+// into accumulator d, smallest products first: nprod = 1 (x0*h0), 2 (x0*h1,
+// x0*h0), 3 (x1*h0, x0*h1, x0*h0) or 6 (x0*h2, x1*h1, x2*h0, x1*h0, x0*h1,
+// x0*h0).  Each product count is its own fixed sequence.
 template <bool BF, int KS>
 __device__ __forceinline__ void issue_products(uint32_t d, uint32_t a_base, int pc, uint64_t b0, uint32_t bpb,
                                                int n, uint32_t idesc, int nprod) {
-    if (nprod == 6) {
-        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 2, true);
-        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 1, 1, false);
-        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 2, 0, false);
+    switch (nprod) {
+        case 1:
+            issue_product<BF, KS, 0, 0, true>(d, a_base, pc, b0, bpb, n, idesc);
+            break;
+        case 2:
+            issue_product<BF, KS, 0, 1, true>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 0, 0, false>(d, a_base, pc, b0, bpb, n, idesc);
+            break;
+        case 3:
+            issue_product<BF, KS, 1, 0, true>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 0, 1, false>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 0, 0, false>(d, a_base, pc, b0, bpb, n, idesc);
+            break;
+        case 6:
+            issue_product<BF, KS, 0, 2, true>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 1, 1, false>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 2, 0, false>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 1, 0, false>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 0, 1, false>(d, a_base, pc, b0, bpb, n, idesc);
+            issue_product<BF, KS, 0, 0, false>(d, a_base, pc, b0, bpb, n, idesc);
+            break;
     }
-    if (nprod >= 3) {
-        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 1, 0, nprod == 3);
-        issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 1, false);
-    }
-    issue_product<BF, KS>(d, a_base, pc, b0, bpb, n, idesc, 0, 0, nprod == 1);
 }
 
 // Split kGroup input values into NP operand parts and write them to the
 // warp's tensor-memory lanes at column c (part p at a_base + p*part_cols).
+// The stores have completed when this returns.
 template <bool BF, int NP>
 __device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int part_cols, int c) {
     if constexpr (!BF) {
@@ -136,8 +153,10 @@ __device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int
             h[e] = tf32_hi_bits(x[e]);
             if constexpr (NP > 1) l[e] = __float_as_uint(x[e] - __uint_as_float(h[e]));
         }
-        ptx::tmem_st_32x32b_x8(a_base + (uint32_t)c, h);
-        if constexpr (NP > 1) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(part_cols + c), l);
+        if constexpr (NP > 1)
+            ptx::tmem_st_x8_sync(a_base + (uint32_t)c, h, a_base + (uint32_t)(part_cols + c), l);
+        else
+            ptx::tmem_st_x8_sync(a_base + (uint32_t)c, h);
     } else {
         uint32_t w[NP][8];
 #pragma unroll
@@ -153,9 +172,55 @@ __device__ __forceinline__ void split_store(const float* x, uint32_t a_base, int
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < NP; ++k) ptx::tmem_st_32x32b_x8(a_base + (uint32_t)(k * part_cols + c / 2), w[k]);
+        const uint32_t a0 = a_base + (uint32_t)(c / 2);
+        if constexpr (NP == 1)
+            ptx::tmem_st_x8_sync(a0, w[0]);
+        else if constexpr (NP == 2)
+            ptx::tmem_st_x8_sync(a0, w[0], a0 + (uint32_t)part_cols, w[1]);
+        else
+            ptx::tmem_st_x8_sync(a0, w[0], a0 + (uint32_t)part_cols, w[1], a0 + (uint32_t)(2 * part_cols), w[2]);
     }
+}
+
+// Split NGR groups of kGroup input values (x[g], written at column c0 + g *
+// cstep) into NP operand parts each and write them all with one fused
+// store-and-wait: the stores have completed when this returns.
+template <bool BF, int NP, int NGR>
+__device__ __forceinline__ void split_store_groups(const float (&x)[NGR][OpFmt<BF>::kGroup], uint32_t a_base,
+                                                   int part_cols, int c0, int cstep) {
+    uint32_t addr[NGR * NP];
+    uint32_t w[NGR * NP][8];
+#pragma unroll
+    for (int g = 0; g < NGR; ++g) {
+        const int c = c0 + cstep * g;
+        if constexpr (!BF) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t h = tf32_hi_bits(x[g][e]);
+                w[g * NP][e] = h;
+                if constexpr (NP > 1) w[g * NP + 1][e] = __float_as_uint(x[g][e] - __uint_as_float(h));
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) addr[g * NP + k] = a_base + (uint32_t)(k * part_cols + c);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float r0a = x[g][2 * e], r0b = x[g][2 * e + 1];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const uint32_t ba = bf16_rn_bits(r0a), bb = bf16_rn_bits(r0b);
+                    w[g * NP + k][e] = ba | (bb << 16);
+                    if (k + 1 < NP) {
+                        r0a -= __uint_as_float(ba << 16);
+                        r0b -= __uint_as_float(bb << 16);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) addr[g * NP + k] = a_base + (uint32_t)(k * part_cols + c / 2);
+        }
+    }
+    ptx::tmem_st_x8_sync_n<NGR * NP>(addr, w);
 }
 
 // Run-time part count (kernels not specialised on it).

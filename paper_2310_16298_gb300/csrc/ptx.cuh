@@ -155,59 +155,32 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
 
-// D[tmem] (+)= A[smem desc] x B[smem desc], TF32 inputs, FP32 accumulate.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// D[tmem] (+)= A[tmem] x B[smem desc], TF32 inputs, FP32 accumulate.  A is
-// read from tensor memory (lane = row of A, one 32-bit column per k).
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// D[tmem] (+)= A[tmem] x B[smem desc], BF16 (or FP16) inputs per the
-// instruction descriptor, FP32 accumulate.  A packs two 16-bit elements per
-// 32-bit tensor-memory column (lower k in the low half).
-__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                           uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// D[tmem] (+)= A x B, BF16 (or FP16) inputs per the instruction descriptor, FP32 accumulate.
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+// D[tmem] (+)= A[tmem] x B[smem desc], FP32 accumulate; A is read from
+// tensor memory (lane = row of A).  KIND_F16: BF16 (or FP16) inputs per the
+// instruction descriptor, two 16-bit elements per 32-bit column (lower k in
+// the low half); else TF32, one element per column.  CLEAR: D = A x B (the
+// first MMA of an accumulation), else D += A x B.  The accumulate choice is
+// part of the instruction text, not a run-time predicate, so a clearing MMA
+// and an accumulating one are never the same asm statement with different
+// operands.
+template <bool KIND_F16, bool CLEAR>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc) {
+    if constexpr (KIND_F16 && CLEAR)
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 0;\n" ::"r"(d_tmem), "r"(a_tmem),
+                     "l"(bdesc), "r"(idesc)
+                     : "memory");
+    else if constexpr (KIND_F16)
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;\n" ::"r"(d_tmem), "r"(a_tmem),
+                     "l"(bdesc), "r"(idesc)
+                     : "memory");
+    else if constexpr (CLEAR)
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 0;\n" ::"r"(d_tmem), "r"(a_tmem),
+                     "l"(bdesc), "r"(idesc)
+                     : "memory");
+    else
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d_tmem), "r"(a_tmem),
+                     "l"(bdesc), "r"(idesc)
+                     : "memory");
 }
 
 // Arrive on `bar` once every tcgen05.mma issued so far by this thread has completed.
@@ -217,41 +190,184 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 32 lanes x 16 consecutive 32-bit columns: thread t of the warp receives lane (base + t).
-__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+// Tensor-memory loads and stores complete asynchronously: tcgen05.ld writes
+// its destination registers, and tcgen05.st reads its source registers, some
+// time after the instruction issues, until tcgen05.wait::ld / ::st.  The
+// compiler cannot see that, so if the load, the store and the wait were
+// separate asm statements it could copy, spill or reuse those registers in
+// between (under register pressure it does).  Every load and store here is
+// therefore fused with its wait in one asm statement: the outputs are
+// defined, and the inputs released, only once the transfer has completed.
+//
+// tmem_ld_xW_sync(a0, r0, a1, r1, ...): 32 lanes x W consecutive 32-bit
+// columns from each address; thread t of the warp receives lane (base + t).
+__device__ __forceinline__ void tmem_ld_x8_sync(uint32_t a0, uint32_t (&r0)[8]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-// 32 lanes x 4 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_ld_32x32b_x4(uint32_t taddr, uint32_t (&r)[4]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-}
-
-// 32 lanes x 8 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
-
-// 32 lanes x 8 consecutive 32-bit columns: thread t of the warp writes lane (base + t).
-__device__ __forceinline__ void tmem_st_32x32b_x8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7])
+        : "r"(a0)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld_x8_sync(uint32_t a0, uint32_t (&r0)[8], uint32_t a1, uint32_t (&r1)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7])
+        : "r"(a0), "r"(a1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x8_sync(uint32_t a0, uint32_t (&r0)[8], uint32_t a1, uint32_t (&r1)[8], uint32_t a2, uint32_t (&r2)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r2[4]), "=r"(r2[5]), "=r"(r2[6]), "=r"(r2[7])
+        : "r"(a0), "r"(a1), "r"(a2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x8_sync(uint32_t a0, uint32_t (&r0)[8], uint32_t a1, uint32_t (&r1)[8], uint32_t a2, uint32_t (&r2)[8], uint32_t a3, uint32_t (&r3)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%34];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%35];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r2[4]), "=r"(r2[5]), "=r"(r2[6]), "=r"(r2[7]), "=r"(r3[0]), "=r"(r3[1]), "=r"(r3[2]), "=r"(r3[3]), "=r"(r3[4]), "=r"(r3[5]), "=r"(r3[6]), "=r"(r3[7])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16_sync(uint32_t a0, uint32_t (&r0)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]), "=r"(r0[15])
+        : "r"(a0)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16_sync(uint32_t a0, uint32_t (&r0)[16], uint32_t a1, uint32_t (&r1)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]), "=r"(r0[15]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]), "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]), "=r"(r1[15])
+        : "r"(a0), "r"(a1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16_sync(uint32_t a0, uint32_t (&r0)[16], uint32_t a1, uint32_t (&r1)[16], uint32_t a2, uint32_t (&r2)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]), "=r"(r0[15]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]), "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]), "=r"(r1[15]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r2[4]), "=r"(r2[5]), "=r"(r2[6]), "=r"(r2[7]), "=r"(r2[8]), "=r"(r2[9]), "=r"(r2[10]), "=r"(r2[11]), "=r"(r2[12]), "=r"(r2[13]), "=r"(r2[14]), "=r"(r2[15])
+        : "r"(a0), "r"(a1), "r"(a2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16_sync(uint32_t a0, uint32_t (&r0)[16], uint32_t a1, uint32_t (&r1)[16], uint32_t a2, uint32_t (&r2)[16], uint32_t a3, uint32_t (&r3)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]), "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]), "=r"(r0[15]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]), "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]), "=r"(r1[15]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r2[4]), "=r"(r2[5]), "=r"(r2[6]), "=r"(r2[7]), "=r"(r2[8]), "=r"(r2[9]), "=r"(r2[10]), "=r"(r2[11]), "=r"(r2[12]), "=r"(r2[13]), "=r"(r2[14]), "=r"(r2[15]), "=r"(r3[0]), "=r"(r3[1]), "=r"(r3[2]), "=r"(r3[3]), "=r"(r3[4]), "=r"(r3[5]), "=r"(r3[6]), "=r"(r3[7]), "=r"(r3[8]), "=r"(r3[9]), "=r"(r3[10]), "=r"(r3[11]), "=r"(r3[12]), "=r"(r3[13]), "=r"(r3[14]), "=r"(r3[15])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+        : "memory");
+}
+
+// tmem_st_x8_sync(a0, v0, ...): 32 lanes x 8 consecutive 32-bit columns at
+// each address; thread t of the warp writes lane (base + t).
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8], uint32_t a1, const uint32_t (&v1)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%10, %11, %12, %13, %14, %15, %16, %17};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(a1), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7]), "r"(v1[0]), "r"(v1[1]), "r"(v1[2]), "r"(v1[3]), "r"(v1[4]), "r"(v1[5]), "r"(v1[6]), "r"(v1[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8], uint32_t a1, const uint32_t (&v1)[8], uint32_t a2, const uint32_t (&v2)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%3, %4, %5, %6, %7, %8, %9, %10};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%11, %12, %13, %14, %15, %16, %17, %18};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%2], {%19, %20, %21, %22, %23, %24, %25, %26};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(a1), "r"(a2), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7]), "r"(v1[0]), "r"(v1[1]), "r"(v1[2]), "r"(v1[3]), "r"(v1[4]), "r"(v1[5]), "r"(v1[6]), "r"(v1[7]), "r"(v2[0]), "r"(v2[1]), "r"(v2[2]), "r"(v2[3]), "r"(v2[4]), "r"(v2[5]), "r"(v2[6]), "r"(v2[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8], uint32_t a1, const uint32_t (&v1)[8], uint32_t a2, const uint32_t (&v2)[8], uint32_t a3, const uint32_t (&v3)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%4, %5, %6, %7, %8, %9, %10, %11};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%12, %13, %14, %15, %16, %17, %18, %19};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%2], {%20, %21, %22, %23, %24, %25, %26, %27};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%3], {%28, %29, %30, %31, %32, %33, %34, %35};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7]), "r"(v1[0]), "r"(v1[1]), "r"(v1[2]), "r"(v1[3]), "r"(v1[4]), "r"(v1[5]), "r"(v1[6]), "r"(v1[7]), "r"(v2[0]), "r"(v2[1]), "r"(v2[2]), "r"(v2[3]), "r"(v2[4]), "r"(v2[5]), "r"(v2[6]), "r"(v2[7]), "r"(v3[0]), "r"(v3[1]), "r"(v3[2]), "r"(v3[3]), "r"(v3[4]), "r"(v3[5]), "r"(v3[6]), "r"(v3[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8], uint32_t a1, const uint32_t (&v1)[8], uint32_t a2, const uint32_t (&v2)[8], uint32_t a3, const uint32_t (&v3)[8], uint32_t a4, const uint32_t (&v4)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%5, %6, %7, %8, %9, %10, %11, %12};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%13, %14, %15, %16, %17, %18, %19, %20};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%2], {%21, %22, %23, %24, %25, %26, %27, %28};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%3], {%29, %30, %31, %32, %33, %34, %35, %36};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%4], {%37, %38, %39, %40, %41, %42, %43, %44};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7]), "r"(v1[0]), "r"(v1[1]), "r"(v1[2]), "r"(v1[3]), "r"(v1[4]), "r"(v1[5]), "r"(v1[6]), "r"(v1[7]), "r"(v2[0]), "r"(v2[1]), "r"(v2[2]), "r"(v2[3]), "r"(v2[4]), "r"(v2[5]), "r"(v2[6]), "r"(v2[7]), "r"(v3[0]), "r"(v3[1]), "r"(v3[2]), "r"(v3[3]), "r"(v3[4]), "r"(v3[5]), "r"(v3[6]), "r"(v3[7]), "r"(v4[0]), "r"(v4[1]), "r"(v4[2]), "r"(v4[3]), "r"(v4[4]), "r"(v4[5]), "r"(v4[6]), "r"(v4[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x8_sync(uint32_t a0, const uint32_t (&v0)[8], uint32_t a1, const uint32_t (&v1)[8], uint32_t a2, const uint32_t (&v2)[8], uint32_t a3, const uint32_t (&v3)[8], uint32_t a4, const uint32_t (&v4)[8], uint32_t a5, const uint32_t (&v5)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%6, %7, %8, %9, %10, %11, %12, %13};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%14, %15, %16, %17, %18, %19, %20, %21};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%2], {%22, %23, %24, %25, %26, %27, %28, %29};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%3], {%30, %31, %32, %33, %34, %35, %36, %37};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%4], {%38, %39, %40, %41, %42, %43, %44, %45};\n"
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%5], {%46, %47, %48, %49, %50, %51, %52, %53};\n"
+        "tcgen05.wait::st.sync.aligned;\n"
+        :
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(v0[0]), "r"(v0[1]), "r"(v0[2]), "r"(v0[3]), "r"(v0[4]), "r"(v0[5]), "r"(v0[6]), "r"(v0[7]), "r"(v1[0]), "r"(v1[1]), "r"(v1[2]), "r"(v1[3]), "r"(v1[4]), "r"(v1[5]), "r"(v1[6]), "r"(v1[7]), "r"(v2[0]), "r"(v2[1]), "r"(v2[2]), "r"(v2[3]), "r"(v2[4]), "r"(v2[5]), "r"(v2[6]), "r"(v2[7]), "r"(v3[0]), "r"(v3[1]), "r"(v3[2]), "r"(v3[3]), "r"(v3[4]), "r"(v3[5]), "r"(v3[6]), "r"(v3[7]), "r"(v4[0]), "r"(v4[1]), "r"(v4[2]), "r"(v4[3]), "r"(v4[4]), "r"(v4[5]), "r"(v4[6]), "r"(v4[7]), "r"(v5[0]), "r"(v5[1]), "r"(v5[2]), "r"(v5[3]), "r"(v5[4]), "r"(v5[5]), "r"(v5[6]), "r"(v5[7])
+        : "memory");
+}
+
+// tmem_st_x8_sync over an array of S stores (compile-time S = 1..6): one asm
+// statement, one wait.
+template <int S>
+__device__ __forceinline__ void tmem_st_x8_sync_n(const uint32_t (&a)[S], const uint32_t (&v)[S][8]) {
+    static_assert(S >= 1 && S <= 6, "1..6 stores");
+    if constexpr (S == 1) tmem_st_x8_sync(a[0], v[0]);
+    if constexpr (S == 2) tmem_st_x8_sync(a[0], v[0], a[1], v[1]);
+    if constexpr (S == 3) tmem_st_x8_sync(a[0], v[0], a[1], v[1], a[2], v[2]);
+    if constexpr (S == 4) tmem_st_x8_sync(a[0], v[0], a[1], v[1], a[2], v[2], a[3], v[3]);
+    if constexpr (S == 5) tmem_st_x8_sync(a[0], v[0], a[1], v[1], a[2], v[2], a[3], v[3], a[4], v[4]);
+    if constexpr (S == 6) tmem_st_x8_sync(a[0], v[0], a[1], v[1], a[2], v[2], a[3], v[3], a[4], v[4], a[5], v[5]);
+}
 
 // Shared-memory matrix descriptor, no swizzle (canonical K-major layout of
 // 8-row x 16-byte core matrices): start address, LBO = byte distance between

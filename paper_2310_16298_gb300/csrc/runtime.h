@@ -31,6 +31,9 @@ struct stencil_plan_s {
     void* scratch = nullptr;
     cudaStream_t stream = nullptr;  // for stencil_submit
     stx::MxPlan* mx = nullptr;
+    uint64_t id = 0;                // unique per plan (tickets refer to plans by id)
+    unsigned int host_error = 0;    // error bits raised on the host (stencil_plan_raise_error)
+    void* staging = nullptr;        // device grid of stencil_apply_host (allocated on first use)
 };
 
 
@@ -46,5 +49,13 @@ cudaError_t run_sweep(const stencil_plan_s* p, const void* src, void* dst, int t
 // Advance d_in by `steps` into d_out on stream s, ping-ponging through `scratch`.
 stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out, int64_t steps, cudaStream_t s,
                          void* scratch);
+
+// Error bits of a plan: a kernel that gave up a bounded wait (the host-mapped
+// word of the matrixized kernels) or bits raised on the host.  Sticky until
+// the plan is destroyed.
+unsigned int plan_error_bits(const stencil_plan_s* p);
+// STENCIL_OK, or STENCIL_ECUDA with a message naming `where`, when the plan's
+// error bits are set.
+stencil_status plan_error_status(const stencil_plan_s* p, const char* where);
 
 }  // namespace stx

@@ -3,7 +3,9 @@
 // Requests (any 2D/3D problem the library accepts, each with its own step
 // count) are queued by stencil_server_submit.  A worker thread admits them in
 // arrival order while the HBM budget and the resident-slot limit allow,
-// allocates their device state (two grid copies plus the plan), and keeps
+// allocates their device state (one grid plus the plan, whose scratch grid is
+// the second copy of the ping-pong: the request's grid is advanced in place),
+// and keeps
 // every resident request moving: each one advances by at most `quantum` time
 // steps per issue on one of several CUDA streams, so the work of many
 // requests overlaps on the device, and a request that arrives while others
@@ -54,8 +56,7 @@ struct Request {
     // state
     enum State { QUEUED, RESIDENT, DONE, FAILED } state = QUEUED;  // written under the server lock
     stencil_plan_t plan = nullptr;
-    void* grid[2] = {nullptr, nullptr};
-    int cur = 0;
+    void* grid = nullptr;  // the request's field, advanced in place
     int64_t done_steps = 0;
     int stream = 0;
     cudaEvent_t ev = nullptr;
@@ -113,14 +114,13 @@ stencil_status admit(stencil_server_s* S, Request* q) {
     if (st == STENCIL_OK) {
         q->used_impl = q->plan->impl;
         cudaStream_t s = S->streams[q->stream];
-        cudaError_t e = cudaMallocAsync(&q->grid[0], q->grid_bytes, s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&q->grid[1], q->grid_bytes, s);
+        cudaError_t e = cudaMallocAsync(&q->grid, q->grid_bytes, s);
         if (e == cudaSuccess) {
             if (q->h_in) {
-                e = cudaMemcpyAsync(q->grid[0], q->h_in, q->grid_bytes, cudaMemcpyHostToDevice, s);
+                e = cudaMemcpyAsync(q->grid, q->h_in, q->grid_bytes, cudaMemcpyHostToDevice, s);
             } else {
                 int64_t count = q->grid_bytes / dtype_size(q->dtype);
-                e = fill_uniform(q->grid[0], q->dtype == STENCIL_F64, count, q->seed, 0, q->lo, q->hi, s);
+                e = fill_uniform(q->grid, q->dtype == STENCIL_F64, count, q->seed, 0, q->lo, q->hi, s);
             }
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
@@ -141,16 +141,15 @@ stencil_status admit(stencil_server_s* S, Request* q) {
 // back now; the plan (and the rest of the charge) goes to the graveyard.
 int64_t release(stencil_server_s* S, Request* q) {
     cudaStream_t s = S->streams[q->stream];
-    for (int k = 0; k < 2; ++k)
-        if (q->grid[k]) {
-            cudaFreeAsync(q->grid[k], s);
-            q->grid[k] = nullptr;
-        }
+    if (q->grid) {
+        cudaFreeAsync(q->grid, s);
+        q->grid = nullptr;
+    }
     if (q->ev) {
         cudaEventDestroy(q->ev);
         q->ev = nullptr;
     }
-    const int64_t grids = 2 * (int64_t)q->grid_bytes;
+    const int64_t grids = (int64_t)q->grid_bytes;
     if (q->plan) {
         S->graveyard.emplace_back(q->plan, (int64_t)q->charge - grids);
         q->plan = nullptr;
@@ -222,6 +221,12 @@ void worker_loop(stencil_server_s* S) {
                     finished.push_back(q);
                     continue;
                 }
+                if (plan_error_status(q->plan, "request work") != STENCIL_OK) {
+                    q->error = STENCIL_ECUDA;
+                    q->message = last_error_string();
+                    finished.push_back(q);
+                    continue;
+                }
                 if (q->draining) {
                     finished.push_back(q);
                     continue;
@@ -230,19 +235,18 @@ void worker_loop(stencil_server_s* S) {
             cudaStream_t s = S->streams[q->stream];
             if (q->done_steps < q->steps) {
                 const int64_t k = std::min<int64_t>(S->quantum, q->steps - q->done_steps);
-                stencil_status st = stencil_apply(q->plan, q->grid[q->cur], q->grid[q->cur ^ 1], k, (stencil_stream_t)s);
+                stencil_status st = stencil_apply(q->plan, q->grid, q->grid, k, (stencil_stream_t)s);
                 if (st != STENCIL_OK) {
                     q->error = st;
                     q->message = last_error_string();
                     finished.push_back(q);
                     continue;
                 }
-                q->cur ^= 1;
                 q->done_steps += k;
                 S->issued += 1;
             } else {
                 // all steps issued: bring the result home
-                cudaMemcpyAsync(q->result, q->grid[q->cur], q->grid_bytes, cudaMemcpyDeviceToHost, s);
+                cudaMemcpyAsync(q->result, q->grid, q->grid_bytes, cudaMemcpyDeviceToHost, s);
                 q->draining = true;
             }
             cudaEventRecord(q->ev, s);
@@ -322,7 +326,7 @@ extern "C" stencil_status stencil_server_submit(stencil_server_t S, const stenci
     q->hi = rq->hi;
     q->steps = rq->steps;
     q->grid_bytes = (size_t)pts * dtype_size(rq->dtype);
-    q->charge = 3 * q->grid_bytes + (1 << 20);  // two grid copies, the plan's scratch grid, operands
+    q->charge = 2 * q->grid_bytes + (1 << 20);  // the request's grid, the plan's scratch grid, operands
     if ((int64_t)q->charge > S->budget) return fail(STENCIL_ENOMEM, "request larger than the whole budget");
     std::lock_guard<std::mutex> lk(S->mu);
     q->id = S->next_id++;

@@ -15,10 +15,11 @@ itself only ever sees interior arithmetic:
                      symmetric C^g; ``corrected=True`` pairs C^o column j with
                      input columns starting at 2r-j (see the readings of the
                      paper in the design notes).
-* ``algorithm1``  -- Algorithm 1 (3D box): groups of ui x uk subblocks BM
-                     (n x n, rows along j, columns along k) accumulated plane
-                     by plane from coefficient vectors CV_{io,ko} and input
-                     vectors AV.
+* ``algorithm1``  -- the blocked 3D update of Sec. 3.4 / Algorithm 1 (box):
+                     groups of ui x uk n x n subblocks, each the sum over the
+                     (z, x) offsets of a banded coefficient matrix times the
+                     shifted input rows (a sum of outer products), written as
+                     matrix algebra rather than in the listing's loop order.
 """
 from __future__ import annotations
 
@@ -102,44 +103,46 @@ def final_2d(a: np.ndarray, r: int, cg: np.ndarray, bc: str, steps: int, n: int,
     return a
 
 
+def banded_coefficients(cg: np.ndarray, a: int, c: int, n: int) -> np.ndarray:
+    """The n x (n + 2r) coefficient matrix of one (z offset a, x offset c)
+    pair: column j' holds the coefficient vector that input row j' of a
+    subblock's slab scatters to the n output rows (output row jj receives
+    input row jj + b with weight C^g[a, b, c], b = 0..2r)."""
+    w = cg.shape[0]
+    v = np.zeros((n, n + w - 1))
+    for b in range(w):
+        v[np.arange(n), np.arange(n) + b] = cg[a, b, c]
+    return v
+
+
 def algorithm1(a: np.ndarray, r: int, cg: np.ndarray, bc: str, steps: int, n: int,
                ui: int, uk: int) -> np.ndarray:
-    """Algorithm 1 over every group of ui x uk subblocks of a 3D grid whose
-    sides are multiples of (ui, n, uk*n)."""
+    """The blocked 3D update of Sec. 3.4 and Algorithm 1, restated as matrix
+    algebra: the output is cut into groups of ui planes x n rows x uk n-wide
+    column subblocks; each n x n subblock of output plane i is the sum, over
+    the z offsets a and x offsets c, of the banded coefficient matrix of (a, c)
+    times the n + 2r input rows of plane i + a - r shifted by c - r columns,
+    i.e. a sum of (coefficient vector) x (input row vector) outer products.
+    The grid sides must be multiples of (ui, n, uk n)."""
     nz, ny, nx = a.shape
     assert nz % ui == 0 and ny % n == 0 and nx % (uk * n) == 0
+    w = 2 * r + 1
+    vs = {(za, xc): banded_coefficients(cg, za, xc, n) for za in range(w) for xc in range(w)}
     for _ in range(steps):
         p = pad(a, r, bc)
         b = np.empty_like(a)
         for i0 in range(0, nz, ui):
             for j0 in range(0, ny, n):
                 for k0 in range(0, nx, uk * n):
-                    BM = np.zeros((ui, uk, n, n))
-                    for j in range(-r, n + r):
-                        # coefficient vectors for this input plane: output rows
-                        # jj receive input row j with weight C^g[r-io, r+j-jj, r+ko]
-                        CV = {}
-                        for io in range(-r, r + 1):
-                            for ko in range(-r, r + 1):
-                                v = np.zeros(n)
-                                for jj in range(n):
-                                    t = r + j - jj
-                                    if 0 <= t <= 2 * r:
-                                        v[jj] = cg[r - io, t, r + ko]
-                                CV[io, ko] = v
-                        for i in range(-r, ui + r):
-                            # padded coordinates: plane i0+i+r, row j0+j+r,
-                            # columns k0 - r .. k0 + uk*n + r - 1
-                            row = p[i0 + i + r, j0 + j + r, k0: k0 + uk * n + 2 * r]
-                            for ko in range(-r, r + 1):
-                                for k in range(uk):
-                                    s = k * n + ko + r
-                                    AV = row[s:s + n]
-                                    for io in range(-r, r + 1):
-                                        if 0 <= i + io < ui:
-                                            BM[i + io, k] += np.outer(CV[io, ko], AV)
+                    # padded input slab of the group: planes i0-r .., rows j0-r .., columns k0-r ..
+                    slab = p[i0:i0 + ui + 2 * r, j0:j0 + n + 2 * r, k0:k0 + uk * n + 2 * r]
                     for i in range(ui):
                         for k in range(uk):
-                            b[i0 + i, j0:j0 + n, k0 + k * n: k0 + (k + 1) * n] = BM[i, k]
+                            bm = np.zeros((n, n))
+                            for za in range(w):
+                                for xc in range(w):
+                                    rows = slab[i + za, :, k * n + xc: k * n + xc + n]
+                                    bm += vs[za, xc] @ rows
+                            b[i0 + i, j0:j0 + n, k0 + k * n: k0 + (k + 1) * n] = bm
         a = b
     return a

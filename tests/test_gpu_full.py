@@ -1,0 +1,126 @@
+"""GPU parity of the matrixized kernels at sizes where every CTA processes
+many tiles (2D) or work units (3D), element by element against the FP64
+oracle (Eq. (stencil-2d9p)).
+
+The persistent kernels launch one CTA per SM and hand tiles out at run time,
+so only grids with several times more tiles than SMs exercise what the large
+workloads run: the wrap-around of the input-stage, A-stage, accumulator-set
+and tile rings, the phase-parity flips of their barriers, the alternation of
+the two MMA issuers over many items, and the reset of the tile counter
+between back-to-back launches (several time steps per test)."""
+import numpy as np
+import pytest
+
+import oracle
+import stencil_inputs as si
+from gpuutil import TOL, check, run
+
+pytestmark = pytest.mark.gpu
+
+
+def num_sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def tiles_2d(shape, r):
+    """Tiles of the 2D kernel: 32 columns x 4 quarters of 2 (32 - 2 ceil(r/2)) rows."""
+    rows = 4 * 2 * (32 - 2 * ((r + 1) // 2))
+    return -(-shape[1] // 32) * -(-shape[0] // rows)
+
+
+def problem(shape, r, kind, seed, lo=0.0, hi=1.0):
+    cg = si.coeffs_random(len(shape), r, kind, 500 + seed, dtype="f32")
+    a = si.round_to(si.field_uniform(shape, 500 + seed, lo, hi), "f32")
+    return a, cg
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_mx_2d_2048_r2_box_many_tiles_per_cta(prec, bc):
+    shape, r, steps = (2048, 2048), 2, 4
+    assert tiles_2d(shape, r) >= 3 * num_sms()
+    a, cg = problem(shape, r, "box", 1)
+    got, info = run(a, r, "box", cg, "f32", bc, steps, impl="matrixized", prec=prec)
+    assert info["impl"] == 2
+    check(got, oracle.gather(a, r, cg, bc, steps), TOL[prec], f"2048^2 r=2 box {bc} {prec}")
+
+
+@pytest.mark.parametrize("r", [1, 3])
+@pytest.mark.parametrize("kind", ["box", "star"])
+def test_mx_2d_1536x1024_many_tiles_per_cta(r, kind):
+    shape, steps = (1536, 1024), 3
+    assert tiles_2d(shape, r) >= 1.2 * num_sms()
+    a, cg = problem(shape, r, kind, 10 + r)
+    got, info = run(a, r, kind, cg, "f32", "periodic", steps, impl="matrixized", prec="tf32x3")
+    assert info["impl"] == 2
+    check(got, oracle.gather(a, r, cg, "periodic", steps), 1e-5, f"1536x1024 r={r} {kind}")
+
+
+def test_mx_2d_4096_ragged_many_tiles_per_cta():
+    """4100 x 4092: about 13 tiles per SM, a ragged last tile row (4100 is
+    not a multiple of the 240-row tile) and a ragged last column block."""
+    shape, r, steps = (4100, 4092), 2, 3
+    assert tiles_2d(shape, r) >= 10 * num_sms()
+    a, cg = problem(shape, r, "box", 20)
+    got, _ = run(a, r, "box", cg, "f32", "periodic", steps, impl="matrixized", prec="tf32x3")
+    check(got, oracle.gather(a, r, cg, "periodic", steps), 1e-5, "4100x4092 r=2 box")
+
+
+@pytest.mark.parametrize("kind,cover,prec", [
+    ("star", "hybrid", "tf32x3"),
+    ("star", "parallel", "tf32x3"),
+    ("star", "hybrid", "bf16x3"),
+    ("box", "auto", "tf32x3"),
+    ("box", "auto", "bf16x3"),
+])
+def test_mx_3d_more_units_than_sms(kind, cover, prec):
+    """192 x 480 x 256, r = 1: 6 chunks of 32 planes x 4 y tiles x (8 or 16)
+    x tiles = 192 or 384 work units, more than the SMs."""
+    shape, r, steps = (192, 480, 256), 1, 3
+    a, cg = problem(shape, r, kind, 30, lo=-1.0, hi=1.0)
+    got, info = run(a, r, kind, cg, "f32", "dirichlet", steps, impl="matrixized", prec=prec, cover=cover)
+    assert info["impl"] == 2
+    units = 6 * 4 * (256 // info["tile_n"])
+    assert units > num_sms()
+    check(got, oracle.gather(a, r, cg, "dirichlet", steps), TOL[prec], f"3d {kind} {cover} {prec}")
+
+
+def workload_problem(shape, r, kind, lo):
+    """The coefficient and field recipe of the 8192^2 (2D) and 512^3 (3D)
+    workloads on a smaller grid."""
+    cg = si.coeffs_random(len(shape), r, kind, 102 if len(shape) == 2 else 103, dtype="f32")
+    a = si.round_to(si.field_uniform(shape, 2 if len(shape) == 2 else 3, lo, 1.0), "f32")
+    return a, cg
+
+
+FULL_RUNS = [((2048, 2048), 2, "box", "periodic", 100, 0.0),
+             ((160, 256, 256), 1, "star", "dirichlet", 50, -1.0),
+             ((160, 256, 256), 1, "box", "dirichlet", 50, -1.0)]
+
+
+@pytest.mark.parametrize("shape,r,kind,bc,steps,lo", FULL_RUNS)
+def test_mx_bf16x2_meets_the_plain_bf16_tolerance_over_full_runs(shape, r, kind, bc, steps, lo):
+    """Over the workloads' full step counts, two-part BF16 on both operands is
+    the cheapest BF16-family mode within the 1e-3 bound set for plain BF16
+    arithmetic (plain BF16 and BF16_W2 drift past it: test below)."""
+    a, cg = workload_problem(shape, r, kind, lo)
+    got, info = run(a, r, kind, cg, "f32", bc, steps, impl="matrixized", prec="bf16x2")
+    assert info["impl"] == 2 and info["prec"] == 4
+    check(got, oracle.gather(a, r, cg, bc, steps), 1e-3, f"bf16x2 {shape} {kind} {steps} steps")
+
+
+@pytest.mark.parametrize("shape,r,kind,bc,steps,lo", FULL_RUNS[:1])
+def test_mx_one_part_bf16_fields_drift_past_1e3_over_full_runs(shape, r, kind, bc, steps, lo):
+    """Rounding the field itself to one BF16 part each step is an error that
+    follows the smooth field (it does not average out), so BF16 and BF16_W2
+    (two-part weights) both exceed 1e-3 after 100 steps; BF16_W2 stays within
+    1e-2, plain BF16 drifts further through its rounded weights' sum."""
+    a, cg = workload_problem(shape, r, kind, lo)
+    want = oracle.gather(a, r, cg, bc, steps)
+    w2, _ = run(a, r, kind, cg, "f32", bc, steps, impl="matrixized", prec="bf16w2")
+    b1, _ = run(a, r, kind, cg, "f32", bc, steps, impl="matrixized", prec="bf16")
+    l2_w2, _ = oracle.error_norms(w2, want)
+    l2_b1, _ = oracle.error_norms(b1, want)
+    assert 1e-3 < l2_w2 <= 1e-2
+    assert l2_b1 > 1e-3

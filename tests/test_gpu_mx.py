@@ -16,7 +16,7 @@ def problem(ndim, shape, r, kind, seed, lo=-1.0, hi=1.0):
     return a, cg
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16x2", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16x2", "bf16", "bf16w2"])
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 @pytest.mark.parametrize("kind", ["box", "star"])
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
@@ -84,7 +84,7 @@ def test_mx_rejects_unaligned_rows():
     assert ei.value.status == sx.EUNSUPPORTED
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16", "bf16w2"])
 @pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("star", 3)])
 @pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
 def test_mx_3d(prec, kind, r, shape):
