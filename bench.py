@@ -247,7 +247,10 @@ def sample_points(shape, r, n=64, n_random=8, seed=77):
     pts = [list(p) for p in np.ndindex(*([2] * ndim))]
     pts = [[0 if b == 0 else shape[d] - 1 for d, b in enumerate(p)] for p in pts]
     seen = {tuple(p) for p in pts}
-    while len(pts) < n:
+    want = min(n, int(np.prod([len(c) for c in cands])))
+    for _ in range(20 * n):   # bounded: small grids hold fewer candidate points
+        if len(pts) >= want:
+            break
         p = tuple(int(rng.choice(c)) for c in cands)
         if p not in seen:
             seen.add(p)

@@ -48,6 +48,7 @@ GatherProblem gather_problem(const stencil_plan_s* p) {
     g.f64 = p->f64;
     g.bc = p->bc;
     g.cg = p->cg.data();
+    g.err = p->err_dev;
     return g;
 }
 
@@ -92,6 +93,7 @@ stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out,
 unsigned int plan_error_bits(const stencil_plan_s* p) {
     unsigned int w = *(volatile const unsigned int*)&p->host_error;
     if (p->mx) w |= mx_device_error(*p->mx);
+    if (p->err_host) w |= *(volatile const unsigned int*)p->err_host;
     return w;
 }
 
@@ -172,6 +174,29 @@ stencil_status ticket_done(uint64_t ticket, const Ticket& t, cudaError_t e) {
 }  // namespace
 
 // =================================================================== plans
+namespace {
+
+// Free everything a plan (complete or half-built) owns.
+void plan_free(stencil_plan_s* p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->scratch) cudaFree(p->scratch);
+    if (p->staging) cudaFree(p->staging);
+    if (p->err_host) cudaFreeHost(p->err_host);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->mx) {
+        mx_plan_free(p->mx);
+        delete p->mx;
+    }
+    delete p;
+}
+
+struct PlanFree {
+    void operator()(stencil_plan_s* p) const { plan_free(p); }
+};
+
+}  // namespace
+
 extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, const int64_t* shape,
                                               int radius, stencil_kind kind, const double* coeffs,
                                               stencil_dtype dtype, const stencil_options* opt) {
@@ -220,7 +245,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     if (o.impl == STENCIL_IMPL_GATHER && prec != STENCIL_PREC_NATIVE)
         return fail(STENCIL_EINVAL, "the gather kernel computes in the storage type (prec NATIVE)");
 
-    std::unique_ptr<stencil_plan_s> p(new stencil_plan_s);
+    std::unique_ptr<stencil_plan_s, PlanFree> p(new stencil_plan_s);
     p->ndim = ndim;
     for (int d = 0; d < ndim; ++d) p->n[d] = shape[d];
     p->r = radius;
@@ -261,6 +286,10 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
 
     // Temporal blocking depth.
     if (p->impl == STENCIL_IMPL_GATHER) {
+        e = cudaHostAlloc((void**)&p->err_host, sizeof(unsigned int), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&p->err_dev, p->err_host, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "error word");
+        *p->err_host = 0;
         p->tb = o.tb > 0 ? o.tb : 1;
         GatherProblem g = gather_problem(p.get());
         int max_smem = 0;
@@ -281,20 +310,13 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
 
     e = cudaMalloc(&p->scratch, p->grid_bytes);
     if (e != cudaSuccess) {
-        if (p->mx) {
-            mx_plan_free(p->mx);
-            delete p->mx;
-        }
+        p->scratch = nullptr;
         cudaGetLastError();
         return fail(STENCIL_ENOMEM, std::string("scratch grid: ") + cudaGetErrorString(e));
     }
     e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-        cudaFree(p->scratch);
-        if (p->mx) {
-            mx_plan_free(p->mx);
-            delete p->mx;
-        }
+        p->stream = nullptr;
         return cuda_fail(e, "cudaStreamCreate");
     }
     plan_register(p.get());
@@ -305,15 +327,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
 extern "C" stencil_status stencil_plan_destroy(stencil_plan_t p) {
     if (!p) return STENCIL_OK;
     plan_unregister(p);
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    if (p->scratch) cudaFree(p->scratch);
-    if (p->staging) cudaFree(p->staging);
-    if (p->stream) cudaStreamDestroy(p->stream);
-    if (p->mx) {
-        mx_plan_free(p->mx);
-        delete p->mx;
-    }
-    delete p;
+    plan_free(p);
     return STENCIL_OK;
 }
 

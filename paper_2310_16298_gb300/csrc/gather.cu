@@ -7,8 +7,25 @@
 // outside the domain are reset to 0 after every sub-step), and writes the
 // tile once.  Each thread computes a strip of RS outputs along the slowest
 // axis, reusing every loaded shared-memory row for all outputs it feeds.
+//
+// Single grids run persistent kernels that stage their tiles with TMA:
+//  * 2D: each CTA walks its tiles with a two-stage shared-memory ring, the
+//    next tile's halo block loading (one cp.async.bulk.tensor, zero fill
+//    outside the grid = the Dirichlet halo) while the current one computes.
+//  * 3D (one step per launch): a work unit is a column of output planes; the
+//    CTA streams its input planes through a ring of 2r+2 plane buffers, each
+//    loaded by TMA while the planes before it are used, so every input plane
+//    is read from global memory once per unit instead of once per 3D tile.
+// With a periodic boundary, tiles whose halo crosses the grid's edge are
+// filled by the element path (indices wrapped); every other tile uses TMA.
+// Waits are bounded; a timeout sets the plan's host-visible error word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "mxutil.cuh"
+#include "ptx.cuh"
 
 namespace stx {
 
@@ -274,6 +291,352 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged persistent kernels (single grids).
+// ---------------------------------------------------------------------------
+constexpr long long kGatherWait = 4000000000LL;   // ~2 s of SM clock per wait
+
+__host__ __device__ constexpr int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity) {
+    return ptx::mbar_wait(bar, parity, kGatherWait);
+}
+
+// 2D tile: TY x TX outputs per tile, threads (32, kBYT), one strip of kRS
+// rows per thread row.  Narrow tiles keep two stages within about 44 KB, so
+// five CTAs share an SM.
+template <typename T>
+struct Tile2 {
+    static constexpr int TY = 64;
+    static constexpr int TX = sizeof(T) == 4 ? 64 : 32;
+    static constexpr int AL = 16 / (int)sizeof(T);   // TMA x granule (16 bytes)
+};
+constexpr int kBYT = 8;
+
+struct G2Args {
+    const void* in;
+    void* out;
+    unsigned int* err;   // host-mapped error word (may be null)
+    int ny, nx, bc, tb;
+    int tiles_x, tiles_total;
+};
+
+// Shared-memory layout of the 2D kernel for depth tb: two stages (TMA ring)
+// and, for tb > 1, a work buffer for the sub-step ping-pong; kRS slack rows
+// after each buffer are read (never used) by ragged strips.
+template <typename T>
+struct Layout2 {
+    int H, HX, SY, SX, buf;   // halo rows, halo columns, rows, columns, elements per buffer
+    __host__ __device__ Layout2(int r, int tb) {
+        H = r * tb;
+        HX = round_up(H, Tile2<T>::AL);
+        SY = Tile2<T>::TY + 2 * H;
+        SX = Tile2<T>::TX + 2 * HX;
+        buf = round_up((SY + kRS) * SX, 128 / (int)sizeof(T));
+    }
+    __host__ __device__ int buffers(int tb) const { return tb > 1 ? 3 : 2; }
+    __host__ __device__ size_t bytes(int tb) const { return (size_t)buffers(tb) * buf * sizeof(T) + 64 + 128; }
+};
+
+// One sub-step of depth t of the 2D tile: src -> dst (or -> the output grid
+// on the last sub-step).  The buffer's element (sy, sx) is grid point
+// (y0 - H + sy, x0 - HX + sx).
+template <typename T, int R, bool STAR>
+__device__ __forceinline__ void substep2(const T* src, T* dst, T* __restrict__ out, const Layout2<T>& L, int t,
+                                         bool last, int64_t ny, int64_t nx, int bc, int64_t y0, int64_t x0,
+                                         const Coeffs<T, ipow(2 * R + 1, 2)>& cf) {
+    constexpr int W = 2 * R + 1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int lo = R * t;                  // rows of the valid region skipped at the top
+    const int lox = L.HX - L.H + R * t;    // columns skipped at the left
+    const int Ht = L.SY - 2 * lo, Wt = L.SX - 2 * lox;
+    const int nstrips = (Ht + kRS - 1) / kRS;
+    for (int strip = ty; strip < nstrips; strip += kBYT) {
+        const int sy0 = lo + strip * kRS;
+        for (int c = tx; c < Wt; c += kBX) {
+            const int sx = lox + c;
+            T acc[kRS];
+#pragma unroll
+            for (int j = 0; j < kRS; ++j) acc[j] = T(0);
+            const T* base = src + (sy0 - R) * L.SX + (sx - R);
+#pragma unroll
+            for (int yi = 0; yi < kRS + 2 * R; ++yi) {
+                T v[W];
+#pragma unroll
+                for (int b = 0; b < W; ++b) v[b] = base[yi * L.SX + b];
+#pragma unroll
+                for (int j = 0; j < kRS; ++j) {
+                    const int a = yi - j;
+                    if (a >= 0 && a < W) {
+#pragma unroll
+                        for (int b = 0; b < W; ++b)
+                            if (!STAR || a == R || b == R) acc[j] = fma(cf.c[a * W + b], v[b], acc[j]);
+                    }
+                }
+            }
+            const int64_t gx = x0 - L.HX + sx;
+#pragma unroll
+            for (int j = 0; j < kRS; ++j) {
+                const int sy = sy0 + j;
+                if (sy < L.SY - lo) {
+                    const int64_t gy = y0 - L.H + sy;
+                    if (last) {
+                        if (gy < ny && gx < nx) out[gy * nx + gx] = acc[j];
+                    } else {
+                        const bool outside = (bc == kBcDirichlet) && (gy < 0 || gy >= ny || gx < 0 || gx >= nx);
+                        dst[sy * L.SX + sx] = outside ? T(0) : acc[j];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Register budgets of the persistent kernels: left alone, the compiler keeps
+// the coefficients and unrolled sums in registers and one CTA fills an SM.
+template <typename T, int NDIM>
+constexpr int min_ctas() { return sizeof(T) == 4 ? (NDIM == 2 ? 3 : 4) : 2; }
+
+template <typename T, int R, bool STAR>
+__global__ void __launch_bounds__(kBX * kBYT, min_ctas<T, 2>())
+gather2d_tma_kernel(const __grid_constant__ CUtensorMap tin, const G2Args a, const Coeffs<T, ipow(2 * R + 1, 2)> cf) {
+    constexpr int TY = Tile2<T>::TY, TX = Tile2<T>::TX;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = (unsigned char*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    const Layout2<T> L(R, a.tb);
+    T* stage[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + L.buf};
+    T* work = reinterpret_cast<T*>(smem_raw) + 2 * L.buf;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)L.buffers(a.tb) * L.buf * sizeof(T));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 2);
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const T* in = (const T*)a.in;
+    T* out = (T*)a.out;
+    const uint32_t box_bytes = (uint32_t)(L.SY * L.SX * sizeof(T));
+    if (tid == 0) {
+        ptx::mbar_init(&full[0], 1);
+        ptx::mbar_init(&full[1], 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    // A tile is staged by TMA unless the boundary is periodic and its halo
+    // block crosses the grid's edge.
+    auto by_tma = [&](int t) {
+        if (a.bc != kBcPeriodic) return true;
+        const int y0 = (t / a.tiles_x) * TY, x0 = (t % a.tiles_x) * TX;
+        return y0 - L.H >= 0 && y0 + TY + L.H <= a.ny && x0 - L.HX >= 0 && x0 + TX + L.HX <= a.nx;
+    };
+    auto issue = [&](int t, int s) {
+        const int y0 = (t / a.tiles_x) * TY, x0 = (t % a.tiles_x) * TX;
+        ptx::mbar_arrive_expect_tx(&full[s], box_bytes);
+        ptx::tma_load_2d(stage[s], &tin, x0 - L.HX, y0 - L.H, &full[s]);
+    };
+    int uses[2] = {0, 0};   // TMA loads into each stage so far (mbarrier phases)
+    int pending = -1;       // stage with a TMA load in flight that nobody waited for yet
+    const int first = blockIdx.x;
+    if (tid == 0 && first < a.tiles_total && by_tma(first)) issue(first, 0);
+    int k = 0;
+    for (int t = first; t < a.tiles_total; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        const int tn = t + gridDim.x;
+        if (tn < a.tiles_total && by_tma(tn)) {
+            if (tid == 0) issue(tn, s ^ 1);
+            pending = s ^ 1;
+        } else {
+            pending = -1;
+        }
+        const int64_t y0 = (int64_t)(t / a.tiles_x) * TY, x0 = (int64_t)(t % a.tiles_x) * TX;
+        if (by_tma(t)) {
+            if (!gwait(&full[s], (uint32_t)(uses[s] & 1))) *abort_flag = 1;
+            ++uses[s];
+        } else {
+            // element path: wrapped indices (periodic boundary)
+            for (int sy = threadIdx.y; sy < L.SY; sy += kBYT)
+                for (int sx = threadIdx.x; sx < L.SX; sx += kBX)
+                    stage[s][sy * L.SX + sx] =
+                        in[wrap_index(y0 - L.H + sy, a.ny) * a.nx + wrap_index(x0 - L.HX + sx, a.nx)];
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        T* bufs[2] = {stage[s], work};
+        for (int st = 1; st <= a.tb; ++st) {
+            substep2<T, R, STAR>(bufs[(st - 1) & 1], bufs[st & 1], out, L, st, st == a.tb, a.ny, a.nx, a.bc, y0, x0, cf);
+            __syncthreads();   // sub-step st is complete (and, after the last, stage s is free)
+        }
+    }
+    if (*abort_flag) {
+        // let a load still in flight land before the CTA gives up its shared memory
+        if (tid == 0 && pending >= 0) ptx::mbar_wait(&full[pending], (uint32_t)(uses[pending] & 1), kGatherWait / 8);
+        if (tid == 0 && a.err) atomicOr(a.err, 2u);
+    }
+}
+
+// 3D streaming kernel: a work unit is TZC output planes of a TY x TX column;
+// its TZC + 2R input planes stream through NPL = 2R + 2 plane buffers.
+template <typename T>
+struct Tile3 {
+    static constexpr int TY = 32;
+    static constexpr int TX = 64;
+    static constexpr int TZC = 64;
+    static constexpr int AL = 16 / (int)sizeof(T);
+};
+constexpr int kThreads3 = 256;   // (TY / kRS) strips x TX columns
+
+struct G3Args {
+    const void* in;
+    void* out;
+    unsigned int* err;
+    int nz, ny, nx, bc;
+    int tiles_x, tiles_y, chunks, units;
+};
+
+template <typename T, int R>
+struct Layout3 {
+    static constexpr int NPL = 2 * R + 2;
+    static constexpr int HX = round_up(R, Tile3<T>::AL);
+    static constexpr int SY = Tile3<T>::TY + 2 * R;
+    static constexpr int SX = Tile3<T>::TX + 2 * HX;
+    static constexpr int PLANE = round_up(SY * SX, 128 / (int)sizeof(T));
+    static constexpr size_t bytes() { return (size_t)NPL * PLANE * sizeof(T) + 8 * NPL + 16 + 128; }
+};
+
+template <typename T, int R, bool STAR>
+__global__ void __launch_bounds__(kThreads3, min_ctas<T, 3>())
+gather3d_stream_kernel(const __grid_constant__ CUtensorMap tin, const G3Args a, const Coeffs<T, ipow(2 * R + 1, 3)> cf) {
+    using L = Layout3<T, R>;
+    constexpr int W = 2 * R + 1, TY = Tile3<T>::TY, TX = Tile3<T>::TX, TZC = Tile3<T>::TZC, NPL = L::NPL;
+    static_assert(TX * (TY / kRS) == kThreads3, "one strip per thread");
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = (unsigned char*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    T* planes = reinterpret_cast<T*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)NPL * L::PLANE * sizeof(T));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(full + NPL);
+    const int tid = threadIdx.x;
+    const T* in = (const T*)a.in;
+    T* out = (T*)a.out;
+    constexpr uint32_t box_bytes = (uint32_t)(L::SY * L::SX * sizeof(T));
+    if (tid == 0) {
+        for (int b = 0; b < NPL; ++b) ptx::mbar_init(&full[b], 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    int uses[NPL];   // TMA loads into each plane buffer so far (mbarrier phases)
+#pragma unroll
+    for (int b = 0; b < NPL; ++b) uses[b] = 0;
+    const int col = tid % TX;            // output column of this thread
+    const int sy0 = (tid / TX) * kRS;    // first output row of its strip
+    unsigned int in_flight = 0;          // buffers with a TMA load nobody waited for yet (bit mask)
+    for (int u = blockIdx.x; u < a.units && !*abort_flag; u += gridDim.x) {
+        const int tx_ = u % a.tiles_x, ty_ = (u / a.tiles_x) % a.tiles_y, tz_ = u / (a.tiles_x * a.tiles_y);
+        const int x0 = tx_ * TX, y0 = ty_ * TY, z0 = tz_ * TZC;
+        const int nout = min(TZC, a.nz - z0);
+        const bool tma = a.bc != kBcPeriodic ||
+                         (y0 - R >= 0 && y0 + TY + R <= a.ny && x0 - L::HX >= 0 && x0 + TX + L::HX <= a.nx);
+        // input plane i of the unit is grid plane z0 - R + i, held in buffer i % NPL
+        auto load = [&](int i) {
+            const int b = i % NPL;
+            int gz = z0 - R + i;
+            if (a.bc == kBcPeriodic) gz = (int)wrap_index(gz, a.nz);
+            if (tma) {
+                if (tid == 0) {
+                    ptx::mbar_arrive_expect_tx(&full[b], box_bytes);
+                    ptx::tma_load_3d(planes + b * L::PLANE, &tin, x0 - L::HX, y0 - R, gz, &full[b]);
+                }
+                in_flight |= 1u << b;
+            } else {
+                T* dst = planes + b * L::PLANE;
+                for (int e = tid; e < L::SY * L::SX; e += kThreads3) {
+                    const int sy = e / L::SX, sx = e % L::SX;
+                    dst[e] = in[((int64_t)gz * a.ny + wrap_index(y0 - R + sy, a.ny)) * a.nx +
+                                wrap_index(x0 - L::HX + sx, a.nx)];
+                }
+            }
+        };
+        auto ready = [&](int i) {   // input plane i is in its buffer
+            const int b = i % NPL;
+            if (tma) {
+                if (!gwait(&full[b], (uint32_t)(uses[b] & 1))) *abort_flag = 1;
+                ++uses[b];
+                in_flight &= ~(1u << b);
+            }
+        };
+        const int nin = nout + 2 * R;
+        for (int i = 0; i < NPL && i < nin; ++i) load(i);
+        if (!tma) __syncthreads();
+        for (int o = 0; o < nout; ++o) {
+            if (o == 0) {
+                for (int i = 0; i < 2 * R + 1; ++i) ready(i);
+            } else {
+                ready(o + 2 * R);
+            }
+            __syncthreads();
+            if (*abort_flag) break;
+            // output plane z0 + o from input planes o .. o + 2R
+            T acc[kRS];
+#pragma unroll
+            for (int j = 0; j < kRS; ++j) acc[j] = T(0);
+            const int sx = L::HX + col;
+#pragma unroll
+            for (int dz = 0; dz < W; ++dz) {
+                const T* pl = planes + ((o + dz) % NPL) * L::PLANE;
+                if (STAR && dz != R) {
+                    const T w = cf.c[(dz * W + R) * W + R];
+#pragma unroll
+                    for (int j = 0; j < kRS; ++j) acc[j] = fma(w, pl[(sy0 + R + j) * L::SX + sx], acc[j]);
+                } else {
+                    const T* base = pl + sy0 * L::SX + (sx - R);
+#pragma unroll
+                    for (int yi = 0; yi < kRS + 2 * R; ++yi) {
+                        T v[W];
+#pragma unroll
+                        for (int b = 0; b < W; ++b) v[b] = base[yi * L::SX + b];
+#pragma unroll
+                        for (int j = 0; j < kRS; ++j) {
+                            const int a1 = yi - j;
+                            if (a1 >= 0 && a1 < W) {
+#pragma unroll
+                                for (int b = 0; b < W; ++b)
+                                    if (!STAR || a1 == R || b == R)
+                                        acc[j] = fma(cf.c[(dz * W + a1) * W + b], v[b], acc[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            const int64_t gz = z0 + o, gx = x0 + col;
+            if (gx < a.nx) {
+#pragma unroll
+                for (int j = 0; j < kRS; ++j) {
+                    const int64_t gy = y0 + sy0 + j;
+                    if (gy < a.ny) out[(gz * a.ny + gy) * a.nx + gx] = acc[j];
+                }
+            }
+            __syncthreads();   // input plane o is no longer needed: its buffer takes plane o + NPL
+            if (o + NPL < nin) {
+                load(o + NPL);
+                if (!tma) __syncthreads();
+            }
+        }
+        // planes loaded but not needed (short last chunk) are waited for before reuse
+        for (int b = 0; b < NPL; ++b)
+            if (in_flight & (1u << b)) {
+                if (!gwait(&full[b], (uint32_t)(uses[b] & 1))) *abort_flag = 1;
+                ++uses[b];
+            }
+        in_flight = 0;
+        __syncthreads();
+    }
+    if (*abort_flag) {
+        if (tid == 0) {
+            for (int b = 0; b < NPL; ++b)
+                if (in_flight & (1u << b)) ptx::mbar_wait(&full[b], (uint32_t)(uses[b] & 1), kGatherWait / 8);
+            if (a.err) atomicOr(a.err, 2u);
+        }
+    }
+}
+
 // Tile shapes.
 constexpr int k2BY = 8, k2TX = 128, k2TY = 64;
 constexpr int k3BY = 8, k3TX = 32, k3TY = 16, k3TZ = 8;
@@ -293,7 +656,7 @@ size_t gather_smem_bytes_t(int ndim, int r, int tb) {
 }
 
 template <typename T, int R, bool STAR>
-cudaError_t launch2d(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
+cudaError_t launch2d_tiles(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
     constexpr int NC = ipow(2 * R + 1, 2);
     Coeffs<T, NC> cf;
     for (int i = 0; i < NC; ++i) cf.c[i] = (T)p.cg[i];
@@ -307,7 +670,7 @@ cudaError_t launch2d(const GatherProblem& p, const void* in, void* out, int tb, 
 }
 
 template <typename T, int R, bool STAR>
-cudaError_t launch3d(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
+cudaError_t launch3d_tiles(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
     constexpr int NC = ipow(2 * R + 1, 3);
     Coeffs<T, NC> cf;
     for (int i = 0; i < NC; ++i) cf.c[i] = (T)p.cg[i];
@@ -318,6 +681,118 @@ cudaError_t launch3d(const GatherProblem& p, const void* in, void* out, int tb, 
     dim3 grid((unsigned)((p.n[2] + k3TX - 1) / k3TX), (unsigned)((p.n[1] + k3TY - 1) / k3TY),
               (unsigned)((p.n[0] + k3TZ - 1) / k3TZ));
     kern<<<grid, dim3(kBX, k3BY), smem, s>>>((const T*)in, (T*)out, p.n[0], p.n[1], p.n[2], p.bc, tb, cf);
+    return cudaGetLastError();
+}
+
+int max_smem_optin() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+int sm_count() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
+}
+
+// TMA tiled view of a C-order grid: dims (innermost first) and element type;
+// false when the driver entry point is missing or the encoder rejects it.
+template <typename T>
+bool encode_grid_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims, const cuuint32_t* box) {
+    auto enc = mxu::get_encode();
+    if (!enc) return false;
+    cuuint64_t strides[2];
+    cuuint64_t st = sizeof(T);
+    for (int d = 0; d + 1 < rank; ++d) {
+        st *= dims[d];
+        strides[d] = st;
+    }
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank,
+               const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The TMA kernels need 16-byte aligned grid bases and rows.
+template <typename T>
+bool tma_layout_ok(const GatherProblem& p, const void* in) {
+    const int64_t nx = p.n[p.ndim - 1];
+    return ((uintptr_t)in & 15u) == 0 && (nx * (int64_t)sizeof(T)) % 16 == 0;
+}
+
+template <typename T, int R, bool STAR>
+cudaError_t launch2d(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
+    const Layout2<T> L(R, tb);
+    const size_t smem = L.bytes(tb);
+    if (!tma_layout_ok<T>(p, in) || smem > (size_t)max_smem_optin() || L.SX > 256 || L.SY > 256)
+        return launch2d_tiles<T, R, STAR>(p, in, out, tb, s);
+    constexpr int NC = ipow(2 * R + 1, 2);
+    Coeffs<T, NC> cf;
+    for (int i = 0; i < NC; ++i) cf.c[i] = (T)p.cg[i];
+    G2Args a;
+    a.in = in;
+    a.out = out;
+    a.err = p.err;
+    a.ny = (int)p.n[0];
+    a.nx = (int)p.n[1];
+    a.bc = p.bc;
+    a.tb = tb;
+    a.tiles_x = (a.nx + Tile2<T>::TX - 1) / Tile2<T>::TX;
+    a.tiles_total = a.tiles_x * ((a.ny + Tile2<T>::TY - 1) / Tile2<T>::TY);
+    alignas(64) CUtensorMap tin;
+    const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny};
+    const cuuint32_t box[2] = {(cuuint32_t)L.SX, (cuuint32_t)L.SY};
+    if (!encode_grid_map<T>(&tin, in, 2, dims, box)) return cudaErrorInvalidValue;
+    auto kern = gather2d_tma_kernel<T, R, STAR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBX * kBYT, smem);
+    if (e != cudaSuccess) return e;
+    int grid = sm_count() * (per > 0 ? per : 1);
+    if (grid > a.tiles_total) grid = a.tiles_total;
+    kern<<<grid, dim3(kBX, kBYT), smem, s>>>(tin, a, cf);
+    return cudaGetLastError();
+}
+
+template <typename T, int R, bool STAR>
+cudaError_t launch3d(const GatherProblem& p, const void* in, void* out, int tb, cudaStream_t s) {
+    using L = Layout3<T, R>;
+    const size_t smem = L::bytes();
+    if (tb != 1 || !tma_layout_ok<T>(p, in) || smem > (size_t)max_smem_optin() || L::SX > 256 || L::SY > 256)
+        return launch3d_tiles<T, R, STAR>(p, in, out, tb, s);
+    constexpr int NC = ipow(2 * R + 1, 3);
+    Coeffs<T, NC> cf;
+    for (int i = 0; i < NC; ++i) cf.c[i] = (T)p.cg[i];
+    G3Args a;
+    a.in = in;
+    a.out = out;
+    a.err = p.err;
+    a.nz = (int)p.n[0];
+    a.ny = (int)p.n[1];
+    a.nx = (int)p.n[2];
+    a.bc = p.bc;
+    a.tiles_x = (a.nx + Tile3<T>::TX - 1) / Tile3<T>::TX;
+    a.tiles_y = (a.ny + Tile3<T>::TY - 1) / Tile3<T>::TY;
+    a.chunks = (a.nz + Tile3<T>::TZC - 1) / Tile3<T>::TZC;
+    a.units = a.tiles_x * a.tiles_y * a.chunks;
+    alignas(64) CUtensorMap tin;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+    const cuuint32_t box[3] = {(cuuint32_t)L::SX, (cuuint32_t)L::SY, 1};
+    if (!encode_grid_map<T>(&tin, in, 3, dims, box)) return cudaErrorInvalidValue;
+    auto kern = gather3d_stream_kernel<T, R, STAR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads3, smem);
+    if (e != cudaSuccess) return e;
+    int grid = sm_count() * (per > 0 ? per : 1);
+    if (grid > a.units) grid = a.units;
+    kern<<<grid, kThreads3, smem, s>>>(tin, a, cf);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ struct GatherProblem {
     bool f64;          // storage/compute type FP64 (else FP32)
     int bc;            // kBcDirichlet | kBcPeriodic
     const double* cg;  // host: dense C^g, (2r+1)^ndim, gather orientation
+    unsigned int* err = nullptr;  // device view of the plan's host-mapped error word (bounded waits)
 };
 
 // Advance `in` by `tb` time steps into `out` (distinct buffers).

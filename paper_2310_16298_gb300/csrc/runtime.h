@@ -34,6 +34,8 @@ struct stencil_plan_s {
     uint64_t id = 0;                // unique per plan (tickets refer to plans by id)
     unsigned int host_error = 0;    // error bits raised on the host (stencil_plan_raise_error)
     void* staging = nullptr;        // device grid of stencil_apply_host (allocated on first use)
+    unsigned int* err_host = nullptr;  // host-mapped error word of the gather kernels' bounded waits
+    unsigned int* err_dev = nullptr;
 };
 
 
