@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
                     choices=["box25-8192", "star7-512", "box27-512", "sine7-512", "sine27-512", "jacobi-256",
-                             "batch-1024", "serve-2000", "error-growth"])
+                             "batch-1024", "serve-2000", "error-growth", "cover-study"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
@@ -54,6 +54,7 @@ def parse():
                     help="line cover of star stencils on the matrixized kernel")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f64", action="store_true", help="skip the FP64 leg of the 2D workload")
     return ap.parse_args()
 
 
@@ -421,6 +422,51 @@ def run_error_growth(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cover_study(args):
+    """The line-cover study of the paper's Sec. 5.2 on this GPU: one sweep of a
+    3D star of order 1..3 (512^3 FP32 by default, zero Dirichlet, seeded
+    coefficients) with each cover -- all lines on the tensor cores (parallel)
+    or the contiguous-axis line there and the off-axis weights on the CUDA
+    cores (hybrid) -- and the cover COVER_AUTO picks, for TF32x3 and TF32."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_2310_16298_gb300 as sx
+    import stencil_inputs as si
+    torch.cuda.set_device(local)
+    side = args.side or 512
+    shape = (side, side, side)
+    x = torch.rand(shape, device="cuda") * 2 - 1
+    y = torch.empty_like(x)
+    stream = torch.cuda.Stream()
+    rows = []
+    for r in (1, 2, 3):
+        cg = si.coeffs_random(3, r, si.STAR, 103, dtype="f32")
+        for prec in ("tf32x3", "tf32"):
+            row = {"radius": r, "points": 6 * r + 1, "prec": prec}
+            for cover in ("parallel", "hybrid", "auto"):
+                plan = sx.Plan(shape, r, "star", cg, "f32", bc="dirichlet", impl="matrixized", prec=prec, cover=cover)
+                for _ in range(2):
+                    plan.apply(x, y, 1, stream)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+                for a_, b_ in ev:
+                    a_.record(stream)
+                    plan.apply(x, y, 1, stream)
+                    b_.record(stream)
+                stream.synchronize()
+                ms = float(np.median([a_.elapsed_time(b_) for a_, b_ in ev]))
+                row[cover] = {"ms_per_sweep": ms, "gstencil_s": x.numel() / ms / 1e6,
+                              "n_lines": plan.info["n_lines"], "n_scalar": plan.info["n_scalar"],
+                              "tile_n": plan.info["tile_n"], "cover": plan.info["cover"]}
+                plan.close()
+            rows.append(row)
+    line = {"metric": "line-cover study: GStencil/s of one sweep per cover", "value": None, "unit": "GStencil/s",
+            "workload": f"3D star r=1..3, {side}^3 FP32, zero Dirichlet, matrixized kernel",
+            "covers": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving_workload(args):
     """Poisson arrivals of mixed stencil solves (70% 2D 128^2..4096^2 r=1..3
     star|box, 30% 3D 64^3..384^3 7/27-point, 10% FP64, steps 10..500) served
@@ -515,6 +561,8 @@ def main():
         return run_serving_workload(args)
     if args.workload == "error-growth":
         return run_error_growth(args)
+    if args.workload == "cover-study":
+        return run_cover_study(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_16298_gb300 as sx
@@ -612,6 +660,39 @@ def main():
         oms, _, _ = time_solves(results[other]["plan"], max(2, args.steps // 2), 1)
         results[other]["timing"] = oms
 
+    # --- the paper's own precision (FP64) on the same 2D workload: the CUDA-core
+    # gather kernel (no FP64 tensor-core kind on this GPU), its error at
+    # sampled points and its fraction of the nominal FP64 FMA rate
+    f64_leg = None
+    if (rank == 0 and args.workload == "box25-8192" and p.dtype == "f32" and not args.no_f64):
+        p64 = dataclasses.replace(p, dtype="f64", coeffs=si.coeffs_random(2, p.r, p.kind, 102, dtype="f64"))
+        f64f = p64.field()
+        x64 = torch.tensor(f64f, dtype=torch.float64, device=dev)
+        y64 = torch.empty_like(x64)
+        plan64 = sx.Plan(p64.shape, p64.r, p64.kind, p64.coeffs, "f64", bc=p64.bc, impl="gather")
+        plan64.apply(x64, y64, p64.steps, stream)
+        stream.synchronize()
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        for a_, b_ in fev:
+            a_.record(stream)
+            plan64.apply(x64, y64, p64.steps, stream)
+            b_.record(stream)
+        stream.synchronize()
+        t64 = float(np.median([a_.elapsed_time(b_) for a_, b_ in fev])) / 1e3
+        pts64 = pts[:16]
+        want64 = oracle.sample(f64f, p64.r, p64.coeffs, p64.bc, p64.steps, pts64)
+        got64 = y64[tuple(torch.as_tensor(c, device=dev) for c in pts64.T)].cpu().numpy()
+        l2_64, mx_64 = oracle.error_norms(got64, want64)
+        g64 = p64.updates / t64 / 1e9
+        nterms = int(np.count_nonzero(p64.coeffs))
+        f64_leg = {"impl": "gather", "dtype": "f64", "gstencil_s": g64, "ms_per_solve": t64 * 1e3,
+                   "err_vs_oracle": {"rel_l2": l2_64, "rel_max": mx_64, "points": len(pts64)},
+                   "fp64_tflops": g64 * 2 * nterms / 1e3, "fp64_peak_tflops_nominal": 1.25,
+                   "fp64_frac_of_nominal": g64 * 2 * nterms / 1e3 / 1.25,
+                   "note": "FP64 runs on CUDA-core FMAs (tcgen05 has no FP64 kind); bound by the FP64 FMA rate"}
+        plan64.close()
+        del x64, y64
+
     # --- dominant kernel: one sweep per launch, timed with events on the launching stream
     info = plan.info
     tb = info["tb"]
@@ -667,6 +748,8 @@ def main():
                 d["ms_per_solve_p50"] = float(np.percentile(t, 50) * 1e3)
                 d["ms_per_solve_p99"] = float(np.percentile(t, 99) * 1e3)
             comp[impl] = d
+        if f64_leg:
+            comp["gather_f64"] = f64_leg
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": p.dtype, "data": "synthetic",

@@ -92,9 +92,12 @@ typedef enum {
  * only the contiguous-axis line (and an identity band that returns the input
  * rows) goes to the tensor cores; the 2*ndim*r - 2r off-axis weights are
  * applied on the CUDA cores to those rows in FP32.  Built for 3D stars;
- * 2D stars and box stencils always use PARALLEL. */
+ * 2D stars and box stencils always use PARALLEL.  AUTO for a 3D star times
+ * one sweep of each cover on the plan's own grids when the plan is created
+ * and keeps the faster (the choice is cached per order, precision, boundary
+ * and grid size class); stencil_plan_info reports the cover that runs. */
 typedef enum {
-    STENCIL_COVER_AUTO = 0,      /* library choice (HYBRID for 3D stars)                */
+    STENCIL_COVER_AUTO = 0,      /* library choice (3D stars: the faster, by timing)   */
     STENCIL_COVER_PARALLEL = 1,
     STENCIL_COVER_HYBRID = 2
 } stencil_cover;
@@ -119,7 +122,7 @@ typedef struct {
     int64_t scratch_bytes;/* device scratch owned by the plan                           */
     int32_t device_error; /* error bits: nonzero once a kernel of the plan gave up a
                              bounded wait (or stencil_plan_raise_error set bits)        */
-    int32_t reserved;
+    int32_t cover;        /* stencil_cover the matrixized kernel runs (0 for GATHER)    */
 } stencil_plan_info_t;
 
 /* ---------------------------------------------------------------------------

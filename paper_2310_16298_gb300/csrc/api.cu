@@ -7,10 +7,12 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -195,6 +197,78 @@ struct PlanFree {
     void operator()(stencil_plan_s* p) const { plan_free(p); }
 };
 
+// ----------------------------------------------------------------- cover choice
+// The covers of a 3D star (all lines on the tensor cores, or the contiguous-
+// axis line there and the off-axis weights on the CUDA cores) trade MMA work
+// against epilogue work differently for each order, precision and grid size
+// (Sec. 5.2 measured the same trade on the paper's machine).  The plan times
+// one sweep of each on its own grids and keeps the faster; the result is
+// cached per order, precision, boundary and grid size class.
+std::mutex g_cover_mu;
+std::map<std::tuple<int, int, int, int>, int> g_cover_cache;
+
+// Mean time of three sweeps (after one untimed) of a matrixized plan, in ms;
+// negative when a launch failed.
+float time_mx_sweeps(const MxPlan& m, const void* src, void* dst, cudaStream_t s) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return -1.f;
+    }
+    float ms = -1.f;
+    bool ok = mx_sweep(m, src, dst, 1, s) == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess;
+    for (int k = 0; k < 3 && ok; ++k) ok = mx_sweep(m, src, dst, 1, s) == cudaSuccess;
+    if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess && mx_device_error(m) == 0)
+        ms /= 3.f;
+    else
+        ms = -1.f;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGetLastError();
+    return ms;
+}
+
+int pick_star_cover(const MxRequest& base, size_t grid_bytes, void* scratch, cudaStream_t s) {
+    int64_t pts = base.n[0] * base.n[1] * base.n[2];
+    int lg = 0;
+    while ((int64_t)1 << (lg + 1) <= pts) ++lg;
+    const auto key = std::make_tuple(base.r, base.prec, base.bc, lg);
+    {
+        std::lock_guard<std::mutex> lk(g_cover_mu);
+        auto it = g_cover_cache.find(key);
+        if (it != g_cover_cache.end()) return it->second;
+    }
+    int best = STENCIL_COVER_HYBRID;
+    void* tmp = nullptr;
+    if (cudaMalloc(&tmp, grid_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return best;   // no room to time: the default, not cached
+    }
+    float best_t = 0.f;
+    for (int cover : {STENCIL_COVER_PARALLEL, STENCIL_COVER_HYBRID}) {
+        MxRequest q = base;
+        q.cover = cover;
+        std::string why;
+        if (!mx_supported(q, &why)) continue;
+        MxPlan m;
+        if (mx_plan_build(q, &m, &why) != STENCIL_OK) continue;
+        const float t = time_mx_sweeps(m, scratch, tmp, s);
+        mx_plan_free(&m);
+        if (t > 0.f && (best_t == 0.f || t < best_t)) {
+            best_t = t;
+            best = cover;
+        }
+    }
+    cudaFree(tmp);
+    if (best_t > 0.f) {
+        std::lock_guard<std::mutex> lk(g_cover_mu);
+        g_cover_cache[key] = best;
+    }
+    return best;
+}
+
 }  // namespace
 
 extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, const int64_t* shape,
@@ -283,6 +357,17 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaMalloc(&p->scratch, p->grid_bytes);
+    if (e != cudaSuccess) {
+        p->scratch = nullptr;
+        cudaGetLastError();
+        return fail(STENCIL_ENOMEM, std::string("scratch grid: ") + cudaGetErrorString(e));
+    }
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        p->stream = nullptr;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
 
     // Temporal blocking depth.
     if (p->impl == STENCIL_IMPL_GATHER) {
@@ -298,6 +383,8 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
         if (gather_smem_bytes(g, p->tb) > (size_t)max_smem)
             return fail(STENCIL_EUNSUPPORTED, "temporal block depth too large for shared memory");
     } else {
+        if (ndim == 3 && p->star && o.cover == STENCIL_COVER_AUTO)
+            req.cover = pick_star_cover(req, p->grid_bytes, p->scratch, p->stream);
         p->mx = new MxPlan();
         stencil_status st = mx_plan_build(req, p->mx, &why);
         if (st != STENCIL_OK) {
@@ -306,18 +393,6 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
             return fail(st, "matrixized plan: " + why);
         }
         p->tb = p->mx->tb;
-    }
-
-    e = cudaMalloc(&p->scratch, p->grid_bytes);
-    if (e != cudaSuccess) {
-        p->scratch = nullptr;
-        cudaGetLastError();
-        return fail(STENCIL_ENOMEM, std::string("scratch grid: ") + cudaGetErrorString(e));
-    }
-    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        p->stream = nullptr;
-        return cuda_fail(e, "cudaStreamCreate");
     }
     plan_register(p.get());
     *out = p.release();
@@ -342,6 +417,7 @@ extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_
         info->n_lines = p->mx->n_lines;
         info->n_scalar = p->mx->n_scalar;
         info->tile_n = p->mx->nb;
+        info->cover = p->mx->cover;
     }
     info->device_error = (int32_t)plan_error_bits(p);
     return STENCIL_OK;

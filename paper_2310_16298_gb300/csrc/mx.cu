@@ -654,6 +654,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     uint32_t bpart = 0;
     std::vector<unsigned char> ops = pack_blocks(q.r, blocks, kNb, W, bf, &bpart);
     p->n_lines = 2 * q.r + 1;
+    p->cover = STENCIL_COVER_PARALLEL;
     p->n_scalar = 0;
     const size_t one = ops.size();   // one copy; CTA b reads copy b % kBopCopies
     p->operand_bytes = one * kBopCopies;

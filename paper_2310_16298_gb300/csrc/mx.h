@@ -34,6 +34,7 @@ struct MxPlan {
     int nb = 16;          // output columns per MMA block
     int n_lines = 0;      // lines on the tensor cores
     int n_scalar = 0;     // weights applied on CUDA cores
+    int cover = STENCIL_COVER_PARALLEL;   // line cover the plan runs
     size_t operand_bytes = 0;
     void* d_operands = nullptr;  // banded line operands (device), kernel-specific layout
     void* d_scalars = nullptr;   // scalar-term table (device)

@@ -637,6 +637,7 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     std::vector<unsigned char> ops = pack_bands(r, lines, NB, KW, bf, &bpart);
     p->n_lines = L;
     p->n_scalar = hyb ? 4 * r : 0;
+    p->cover = hyb ? STENCIL_COVER_HYBRID : STENCIL_COVER_PARALLEL;
     p->operand_bytes = ops.size();
     cudaError_t e = cudaMalloc(&p->d_operands, p->operand_bytes);
     if (e != cudaSuccess) {

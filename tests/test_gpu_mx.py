@@ -158,3 +158,40 @@ def test_mx_bf16_exact_operands(prec):
     cg = rng.integers(-8, 9, size=(5, 5)) / 64.0
     got, _ = run(a, 2, "box", cg, "f32", "periodic", 2, impl="matrixized", prec=prec)
     check(got, oracle.gather(a, 2, cg, "periodic", 2), 1e-6, f"{prec} exact operands")
+
+
+def test_mx_cover_auto_picks_a_built_cover_and_matches_it():
+    """COVER_AUTO on a 3D star times both covers and keeps one; the plan
+    reports it, and its result is bit-identical to the explicit plan's."""
+    shape = (40, 120, 64)
+    a, cg = problem(3, shape, 2, "star", seed=71)
+    got, info = run(a, 2, "star", cg, "f32", "dirichlet", 3, impl="matrixized", prec="tf32x3", cover="auto")
+    assert info["cover"] in (1, 2)
+    want, info2 = run(a, 2, "star", cg, "f32", "dirichlet", 3, impl="matrixized", prec="tf32x3",
+                      cover={1: "parallel", 2: "hybrid"}[info["cover"]])
+    assert info2["cover"] == info["cover"]
+    assert np.array_equal(got, want)
+    # 2D plans run the parallel cover; gather plans report none
+    _, i2 = run(a[0], 2, "star", cg[2], "f32", "dirichlet", 1, impl="matrixized")
+    assert i2["cover"] == 1
+    _, ig = run(a[0], 2, "star", cg[2], "f32", "dirichlet", 1, impl="gather")
+    assert ig["cover"] == 0
+
+
+@pytest.mark.parametrize("pattern", ["diagonal", "anti-diagonal", "random", "ring"])
+@pytest.mark.parametrize("impl", ["matrixized", "gather"])
+def test_arbitrary_weight_patterns(pattern, impl):
+    """Weight patterns that are neither star nor box (Sec. 3.3 diagonal lines,
+    Sec. 3.5 arbitrary patterns) run as a box plan whose absent weights are
+    zero: every line of the pattern is a (possibly sparse) banded operand."""
+    r = 2
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0.1, 1.0, size=(5, 5))
+    a_, b_ = np.meshgrid(np.arange(5), np.arange(5), indexing="ij")
+    mask = {"diagonal": a_ == b_, "anti-diagonal": a_ + b_ == 4,
+            "random": rng.uniform(size=(5, 5)) < 0.4,
+            "ring": np.maximum(abs(a_ - 2), abs(b_ - 2)) == 2}[pattern]
+    cg = si.round_to(np.where(mask, w, 0.0) / np.where(mask, w, 0.0).sum(), "f32")
+    a = si.round_to(si.field_uniform((300, 196), 77, -1.0, 1.0), "f32")
+    got, info = run(a, r, "box", cg, "f32", "periodic", 4, impl=impl, prec="tf32x3" if impl == "matrixized" else "native")
+    check(got, oracle.gather(a, r, cg, "periodic", 4), 1e-5, f"{pattern} {impl}")
