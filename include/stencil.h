@@ -15,8 +15,9 @@
  *
  * Conventions for every entry point:
  *  - Arrays are C-ordered, last index contiguous (the footnote of Sec. 4.1),
- *    packed (no row padding), and hold only the interior points listed in
- *    `shape`.  Points outside the interior are 0 at every step
+ *    and hold only the interior points listed in `shape`; rows are packed
+ *    unless the plan was created with a pitch (stencil_options.pitch), which
+ *    then applies to every grid passed to the plan.  Points outside the interior are 0 at every step
  *    (STENCIL_BC_DIRICHLET_ZERO) or the interior taken modulo the extent
  *    (STENCIL_BC_PERIODIC).
  *  - Device pointers are CUDA device (or managed) addresses on the device
@@ -108,7 +109,12 @@ typedef struct {
     int32_t impl;     /* stencil_impl; default AUTO                                            */
     int32_t tb;       /* time steps fused per sweep (temporal blocking); 0 = library choice     */
     int32_t cover;    /* stencil_cover; default AUTO (EINVAL when out of range)                 */
-    int32_t reserved[3];
+    int32_t pitch;    /* row stride of the grids, in elements (0 = packed rows); >= the
+                         contiguous extent and a multiple of 16 bytes, else EINVAL.  Padding
+                         elements are neither read nor written.  Packed grids whose rows are
+                         not 16-byte multiples run on the tensor-core kernels through two
+                         padded grids the plan owns (one strided copy in, one out per apply) */
+    int32_t reserved[2];
 } stencil_options;
 
 /* Plan introspection (filled by stencil_plan_info). */

@@ -47,7 +47,8 @@ class StencilError(RuntimeError):
 
 class stencil_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("bc", ctypes.c_int32), ("impl", ctypes.c_int32),
-                ("tb", ctypes.c_int32), ("cover", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tb", ctypes.c_int32), ("cover", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class stencil_batch_info_t(ctypes.Structure):
@@ -173,13 +174,14 @@ def stencil_version() -> str:
 COVERS = {"auto": 0, "parallel": 1, "hybrid": 2}
 
 
-def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto") -> stencil_options:
+def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto", pitch=0) -> stencil_options:
     o = stencil_options()
     o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     o.bc = BCS[bc] if isinstance(bc, str) else int(bc)
     o.impl = IMPLS[impl] if isinstance(impl, str) else int(impl)
     o.tb = int(tb)
     o.cover = COVERS[cover] if isinstance(cover, str) else int(cover)
+    o.pitch = int(pitch)
     return o
 
 

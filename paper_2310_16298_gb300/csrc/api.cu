@@ -51,6 +51,7 @@ GatherProblem gather_problem(const stencil_plan_s* p) {
     g.bc = p->bc;
     g.cg = p->cg.data();
     g.err = p->err_dev;
+    g.ldx = p->ldx;
     return g;
 }
 
@@ -64,8 +65,33 @@ cudaError_t run_sweep(const stencil_plan_s* p, const void* src, void* dst, int t
 // Time loop (Sec. 2.2: two grid copies used alternately).  The copies are the
 // caller's output and the plan's scratch grid, ordered so that the last
 // sweep writes d_out and no sweep reads the buffer it writes.
+// Strided copy between the caller's layout (row stride pitch) and the padded
+// layout of a repacking plan (row stride ldx).
+cudaError_t repack_copy(const stencil_plan_s* p, void* dst, int64_t dld, const void* src, int64_t sld, cudaStream_t s) {
+    const size_t es = p->f64 ? 8 : 4;
+    const size_t rows = (size_t)(p->points / p->n[p->ndim - 1]);
+    return cudaMemcpy2DAsync(dst, (size_t)dld * es, src, (size_t)sld * es, (size_t)p->n[p->ndim - 1] * es, rows,
+                             cudaMemcpyDeviceToDevice, s);
+}
+
 stencil_status time_loop(const stencil_plan_s* p, const void* d_in, void* d_out, int64_t steps,
                          cudaStream_t s, void* scratch) {
+    if (steps > 0 && p->repack) {
+        // the field goes into the plan's padded grids, is advanced there and comes back
+        void* g[2] = {p->pad, p->scratch};
+        cudaError_t e = repack_copy(p, g[0], p->ldx, d_in, p->pitch, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+        const int tb = p->tb;
+        const int64_t nsweep = (steps + tb - 1) / tb;
+        for (int64_t k = 0; k < nsweep; ++k) {
+            const int depth = (int)((k == nsweep - 1) ? (steps - (nsweep - 1) * tb) : tb);
+            e = run_sweep(p, g[k & 1], g[(k + 1) & 1], depth, s);
+            if (e != cudaSuccess) return cuda_fail(e, "stencil sweep launch");
+        }
+        e = repack_copy(p, d_out, p->pitch, g[nsweep & 1], p->ldx, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+        return STENCIL_OK;
+    }
     if (steps == 0) {
         if (d_in != d_out) {
             cudaError_t e = cudaMemcpyAsync(d_out, d_in, p->grid_bytes, cudaMemcpyDeviceToDevice, s);
@@ -184,6 +210,7 @@ void plan_free(stencil_plan_s* p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->scratch) cudaFree(p->scratch);
     if (p->staging) cudaFree(p->staging);
+    if (p->pad) cudaFree(p->pad);
     if (p->err_host) cudaFreeHost(p->err_host);
     if (p->stream) cudaStreamDestroy(p->stream);
     if (p->mx) {
@@ -290,6 +317,10 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     if (o.tb < 0 || o.tb > 16) return fail(STENCIL_EINVAL, "tb must be in 0..16");
     if (o.cover < STENCIL_COVER_AUTO || o.cover > STENCIL_COVER_HYBRID)
         return fail(STENCIL_EINVAL, "cover out of range");
+    const int64_t es = (dtype == STENCIL_F64) ? 8 : 4;
+    if (o.pitch < 0) return fail(STENCIL_EINVAL, "pitch must be >= 0");
+    if (o.pitch > 0 && (o.pitch < shape[ndim - 1] || (o.pitch * es) % 16 != 0))
+        return fail(STENCIL_EINVAL, "pitch must be at least the contiguous extent and give 16-byte rows");
     const int W = 2 * radius + 1;
     int64_t nco = 1, points = 1;
     for (int d = 0; d < ndim; ++d) {
@@ -328,7 +359,10 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     p->bc = o.bc;
     p->cg.assign(coeffs, coeffs + nco);
     p->points = points;
-    p->grid_bytes = (size_t)points * (f64 ? 8 : 4);
+    const int64_t nlast = shape[ndim - 1];
+    p->pitch = o.pitch > 0 ? o.pitch : nlast;
+    p->grid_bytes = (size_t)(points / nlast) * (size_t)p->pitch * (size_t)es;
+    p->ldx = p->pitch;
 
     // Implementation choice.  For the outer-product kernels, NATIVE means the
     // FP32-accuracy split (TF32X3); FP64 runs on the CUDA-core kernel.
@@ -343,6 +377,10 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     req.cg = p->cg.data();
     req.prec = (prec == STENCIL_PREC_NATIVE) ? STENCIL_PREC_TF32X3 : prec;
     req.tb = o.tb;
+    // The tensor-core kernels stage rows with TMA, which needs 16-byte rows:
+    // packed grids whose rows are not run on padded copies the plan owns.
+    const bool aligned_rows = (p->pitch * es) % 16 == 0;
+    req.ldx = aligned_rows ? p->pitch : (p->pitch + (16 / es) - 1) / (16 / es) * (16 / es);
     req.cover = o.cover;
     const bool mx_ok = (o.impl != STENCIL_IMPL_GATHER) && mx_supported(req, &why);
     const bool want_mx = (o.impl == STENCIL_IMPL_MATRIXIZED) || (prec != STENCIL_PREC_NATIVE);
@@ -350,6 +388,8 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     if (mx_ok) {
         p->impl = STENCIL_IMPL_MATRIXIZED;
         p->prec = req.prec;
+        p->ldx = req.ldx;
+        p->repack = !aligned_rows;
     } else {
         p->impl = STENCIL_IMPL_GATHER;
         p->prec = STENCIL_PREC_NATIVE;
@@ -357,9 +397,12 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    e = cudaMalloc(&p->scratch, p->grid_bytes);
+    // scratch: the second grid of the ping-pong (padded like the kernels' grids
+    // when the plan repacks, and then with a first padded grid beside it)
+    p->pad_bytes = (size_t)(points / nlast) * (size_t)p->ldx * (size_t)es;
+    e = cudaMalloc(&p->scratch, p->repack ? p->pad_bytes : p->grid_bytes);
+    if (e == cudaSuccess && p->repack) e = cudaMalloc(&p->pad, p->pad_bytes);
     if (e != cudaSuccess) {
-        p->scratch = nullptr;
         cudaGetLastError();
         return fail(STENCIL_ENOMEM, std::string("scratch grid: ") + cudaGetErrorString(e));
     }
@@ -384,7 +427,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
             return fail(STENCIL_EUNSUPPORTED, "temporal block depth too large for shared memory");
     } else {
         if (ndim == 3 && p->star && o.cover == STENCIL_COVER_AUTO)
-            req.cover = pick_star_cover(req, p->grid_bytes, p->scratch, p->stream);
+            req.cover = pick_star_cover(req, p->repack ? p->pad_bytes : p->grid_bytes, p->scratch, p->stream);
         p->mx = new MxPlan();
         stencil_status st = mx_plan_build(req, p->mx, &why);
         if (st != STENCIL_OK) {
@@ -412,7 +455,8 @@ extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_
     info->impl = p->impl;
     info->prec = p->prec;
     info->tb = p->tb;
-    info->scratch_bytes = (int64_t)p->grid_bytes + (p->mx ? (int64_t)p->mx->operand_bytes : 0);
+    info->scratch_bytes = (int64_t)(p->repack ? 2 * p->pad_bytes : p->grid_bytes) +
+                          (p->mx ? (int64_t)p->mx->operand_bytes : 0);
     if (p->mx) {
         info->n_lines = p->mx->n_lines;
         info->n_scalar = p->mx->n_scalar;
@@ -513,6 +557,9 @@ extern "C" stencil_status stencil_apply_noalloc(stencil_plan_t p, const void* d_
                                                 stencil_stream_t stream) {
     if (!p || !d_in || !d_out) return fail(STENCIL_EINVAL, "NULL argument");
     if (steps < 0) return fail(STENCIL_EINVAL, "steps must be >= 0");
+    if (p->repack)
+        return fail(STENCIL_EINVAL, "stencil_apply_noalloc: rows that are not 16-byte multiples run on the plan's "
+                                    "padded grids; use stencil_apply or pass a pitch");
     if (p->grid_bytes > kNoAllocScratchBytes)
         return fail(STENCIL_EINVAL, "grid of " + std::to_string(p->grid_bytes) +
                                         " bytes exceeds the 16 MiB static scratch of stencil_apply_noalloc");

@@ -242,10 +242,11 @@ extern "C" stencil_status stencil_batch_create_ex(stencil_batch_t* out, int n, c
         if (!plans[i] || !d_in[i] || !d_out[i] || steps[i] < 0)
             return fail(STENCIL_EINVAL, "invalid entry " + std::to_string(i));
     const stencil_plan_s* p0 = plans[0];
+    // packed launches take 2D plans of one order, kind and dtype with packed rows
     bool packed = (p0->ndim == 2) && p0->r <= 3;
-    for (int i = 1; i < n && packed; ++i) {
+    for (int i = 0; i < n && packed; ++i) {
         const stencil_plan_s* p = plans[i];
-        packed = p->ndim == 2 && p->r == p0->r && p->star == p0->star && p->f64 == p0->f64;
+        packed = p->ndim == 2 && p->r == p0->r && p->star == p0->star && p->f64 == p0->f64 && p->pitch == p->n[1];
     }
     std::unique_ptr<stencil_batch_s, void (*)(stencil_batch_s*)> b(new stencil_batch_s, batch_free);
     b->n = n;

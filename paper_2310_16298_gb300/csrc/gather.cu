@@ -50,25 +50,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Address of a tile element after the boundary rule, or nullptr for a zero.
 template <typename T>
 __device__ __forceinline__ const T* src2(const T* __restrict__ a, int64_t y, int64_t x, int64_t ny,
-                                         int64_t nx, int bc) {
+                                         int64_t nx, int64_t ldx, int bc) {
     if (y < 0 || y >= ny || x < 0 || x >= nx) {
         if (bc == kBcDirichlet) return nullptr;
         y = wrap_index(y, ny);
         x = wrap_index(x, nx);
     }
-    return a + y * nx + x;
+    return a + y * ldx + x;
 }
 
 template <typename T>
 __device__ __forceinline__ const T* src3(const T* __restrict__ a, int64_t z, int64_t y, int64_t x,
-                                         int64_t nz, int64_t ny, int64_t nx, int bc) {
+                                         int64_t nz, int64_t ny, int64_t nx, int64_t ldx, int bc) {
     if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) {
         if (bc == kBcDirichlet) return nullptr;
         z = wrap_index(z, nz);
         y = wrap_index(y, ny);
         x = wrap_index(x, nx);
     }
-    return a + (z * ny + y) * nx + x;
+    return a + (z * ny + y) * ldx + x;
 }
 
 // ---------------------------------------------------------------------------
@@ -78,7 +78,7 @@ __device__ __forceinline__ const T* src3(const T* __restrict__ a, int64_t z, int
 // single-problem and the batched kernels.
 template <typename T, int R, bool STAR, int BY, int TX, int TY>
 __device__ __forceinline__ void gather2d_tile(const T* __restrict__ in, T* __restrict__ out, int64_t ny,
-                                              int64_t nx, int bc, int tb, const Coeffs<T, ipow(2 * R + 1, 2)>& cf,
+                                              int64_t nx, int64_t ldx, int bc, int tb, const Coeffs<T, ipow(2 * R + 1, 2)>& cf,
                                               int64_t y0, int64_t x0, T* smem) {
     constexpr int W = 2 * R + 1;
     const int H = R * tb;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void gather2d_tile(const T* __restrict__ in, T* __res
             const int64_t gx = x0 - H + sx;
             T* d = smem + sy * SX + sx;
             const T* g = nullptr;
-            if (sy < SY) g = interior ? in + gy * nx + gx : src2(in, gy, gx, ny, nx, bc);
+            if (sy < SY) g = interior ? in + gy * ldx + gx : src2(in, gy, gx, ny, nx, ldx, bc);
             if (g) cp_async_elem(d, g);
             else *d = T(0);
         }
@@ -142,7 +142,7 @@ __device__ __forceinline__ void gather2d_tile(const T* __restrict__ in, T* __res
                     if (sy < SY - lo) {
                         const int64_t gy = y0 - H + sy;
                         if (last) {
-                            if (gy < ny && gx < nx) out[gy * nx + gx] = acc[j];
+                            if (gy < ny && gx < nx) out[gy * ldx + gx] = acc[j];
                         } else {
                             const bool outside = (bc == kBcDirichlet) && (gy < 0 || gy >= ny || gx < 0 || gx >= nx);
                             dst[sy * SX + sx] = outside ? T(0) : acc[j];
@@ -157,10 +157,10 @@ __device__ __forceinline__ void gather2d_tile(const T* __restrict__ in, T* __res
 
 template <typename T, int R, bool STAR, int BY, int TX, int TY>
 __global__ void __launch_bounds__(kBX * BY)
-gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64_t nx, int bc,
+gather2d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t ny, int64_t nx, int64_t ldx, int bc,
                 int tb, Coeffs<T, ipow(2 * R + 1, 2)> cf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gather2d_tile<T, R, STAR, BY, TX, TY>(in, out, ny, nx, bc, tb, cf, (int64_t)blockIdx.y * TY,
+    gather2d_tile<T, R, STAR, BY, TX, TY>(in, out, ny, nx, ldx, bc, tb, cf, (int64_t)blockIdx.y * TY,
                                           (int64_t)blockIdx.x * TX, reinterpret_cast<T*>(smem_raw));
 }
 
@@ -185,7 +185,7 @@ gather2d_batch_kernel(const BatchProblem* __restrict__ probs, int nprob, int tot
         Coeffs<T, NC> cf;
 #pragma unroll
         for (int i = 0; i < NC; ++i) cf.c[i] = coef[(size_t)P.coef_index * NC + i];
-        gather2d_tile<T, R, STAR, BY, TX, TY>((const T*)P.src, (T*)P.dst, P.ny, P.nx, P.bc, P.depth, cf,
+        gather2d_tile<T, R, STAR, BY, TX, TY>((const T*)P.src, (T*)P.dst, P.ny, P.nx, P.nx, P.bc, P.depth, cf,
                                               (int64_t)(local / P.tiles_x) * TY, (int64_t)(local % P.tiles_x) * TX,
                                               reinterpret_cast<T*>(smem_raw));
     }
@@ -198,7 +198,7 @@ gather2d_batch_kernel(const BatchProblem* __restrict__ probs, int nprob, int tot
 template <typename T, int R, bool STAR, int BY, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kBX * BY)
 gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64_t ny, int64_t nx,
-                int bc, int tb, Coeffs<T, ipow(2 * R + 1, 3)> cf) {
+                int64_t ldx, int bc, int tb, Coeffs<T, ipow(2 * R + 1, 3)> cf) {
     constexpr int W = 2 * R + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* smem = reinterpret_cast<T*>(smem_raw);
@@ -221,7 +221,7 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
                 const int64_t gx = x0 - H + sx;
                 T* d = smem + sz * plane + sy * SX + sx;
                 const T* g = nullptr;
-                if (sz < SZ) g = interior ? in + (gz * ny + gy) * nx + gx : src3(in, gz, gy, gx, nz, ny, nx, bc);
+                if (sz < SZ) g = interior ? in + (gz * ny + gy) * ldx + gx : src3(in, gz, gy, gx, nz, ny, nx, ldx, bc);
                 if (g) cp_async_elem(d, g);
                 else *d = T(0);
             }
@@ -276,7 +276,7 @@ gather3d_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t nz, int64
                         if (sz < SZ - lo) {
                             const int64_t gz = z0 - H + sz;
                             if (last) {
-                                if (gz < nz && gy < ny && gx < nx) out[(gz * ny + gy) * nx + gx] = acc[j];
+                                if (gz < nz && gy < ny && gx < nx) out[(gz * ny + gy) * ldx + gx] = acc[j];
                             } else {
                                 const bool outside = (bc == kBcDirichlet) &&
                                                      (gz < 0 || gz >= nz || gy < 0 || gy >= ny || gx < 0 || gx >= nx);
@@ -318,6 +318,7 @@ struct G2Args {
     const void* in;
     void* out;
     unsigned int* err;   // host-mapped error word (may be null)
+    int64_t ldx;         // row stride of the grids (elements)
     int ny, nx, bc, tb;
     int tiles_x, tiles_total;
 };
@@ -344,7 +345,7 @@ struct Layout2 {
 // (y0 - H + sy, x0 - HX + sx).
 template <typename T, int R, bool STAR>
 __device__ __forceinline__ void substep2(const T* src, T* dst, T* __restrict__ out, const Layout2<T>& L, int t,
-                                         bool last, int64_t ny, int64_t nx, int bc, int64_t y0, int64_t x0,
+                                         bool last, int64_t ny, int64_t nx, int64_t ldx, int bc, int64_t y0, int64_t x0,
                                          const Coeffs<T, ipow(2 * R + 1, 2)>& cf) {
     constexpr int W = 2 * R + 1;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -382,7 +383,7 @@ __device__ __forceinline__ void substep2(const T* src, T* dst, T* __restrict__ o
                 if (sy < L.SY - lo) {
                     const int64_t gy = y0 - L.H + sy;
                     if (last) {
-                        if (gy < ny && gx < nx) out[gy * nx + gx] = acc[j];
+                        if (gy < ny && gx < nx) out[gy * ldx + gx] = acc[j];
                     } else {
                         const bool outside = (bc == kBcDirichlet) && (gy < 0 || gy >= ny || gx < 0 || gx >= nx);
                         dst[sy * L.SX + sx] = outside ? T(0) : acc[j];
@@ -455,13 +456,14 @@ gather2d_tma_kernel(const __grid_constant__ CUtensorMap tin, const G2Args a, con
             for (int sy = threadIdx.y; sy < L.SY; sy += kBYT)
                 for (int sx = threadIdx.x; sx < L.SX; sx += kBX)
                     stage[s][sy * L.SX + sx] =
-                        in[wrap_index(y0 - L.H + sy, a.ny) * a.nx + wrap_index(x0 - L.HX + sx, a.nx)];
+                        in[wrap_index(y0 - L.H + sy, a.ny) * a.ldx + wrap_index(x0 - L.HX + sx, a.nx)];
         }
         __syncthreads();
         if (*abort_flag) break;
         T* bufs[2] = {stage[s], work};
         for (int st = 1; st <= a.tb; ++st) {
-            substep2<T, R, STAR>(bufs[(st - 1) & 1], bufs[st & 1], out, L, st, st == a.tb, a.ny, a.nx, a.bc, y0, x0, cf);
+            substep2<T, R, STAR>(bufs[(st - 1) & 1], bufs[st & 1], out, L, st, st == a.tb, a.ny, a.nx, a.ldx, a.bc, y0,
+                                 x0, cf);
             __syncthreads();   // sub-step st is complete (and, after the last, stage s is free)
         }
     }
@@ -487,6 +489,7 @@ struct G3Args {
     const void* in;
     void* out;
     unsigned int* err;
+    int64_t ldx;         // row stride of the grids (elements); planes are ny rows
     int nz, ny, nx, bc;
     int tiles_x, tiles_y, chunks, units;
 };
@@ -549,7 +552,7 @@ gather3d_stream_kernel(const __grid_constant__ CUtensorMap tin, const G3Args a, 
                 T* dst = planes + b * L::PLANE;
                 for (int e = tid; e < L::SY * L::SX; e += kThreads3) {
                     const int sy = e / L::SX, sx = e % L::SX;
-                    dst[e] = in[((int64_t)gz * a.ny + wrap_index(y0 - R + sy, a.ny)) * a.nx +
+                    dst[e] = in[((int64_t)gz * a.ny + wrap_index(y0 - R + sy, a.ny)) * a.ldx +
                                 wrap_index(x0 - L::HX + sx, a.nx)];
                 }
             }
@@ -610,7 +613,7 @@ gather3d_stream_kernel(const __grid_constant__ CUtensorMap tin, const G3Args a, 
 #pragma unroll
                 for (int j = 0; j < kRS; ++j) {
                     const int64_t gy = y0 + sy0 + j;
-                    if (gy < a.ny) out[(gz * a.ny + gy) * a.nx + gx] = acc[j];
+                    if (gy < a.ny) out[(gz * a.ny + gy) * a.ldx + gx] = acc[j];
                 }
             }
             __syncthreads();   // input plane o is no longer needed: its buffer takes plane o + NPL
@@ -665,7 +668,7 @@ cudaError_t launch2d_tiles(const GatherProblem& p, const void* in, void* out, in
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((p.n[1] + k2TX - 1) / k2TX), (unsigned)((p.n[0] + k2TY - 1) / k2TY));
-    kern<<<grid, dim3(kBX, k2BY), smem, s>>>((const T*)in, (T*)out, p.n[0], p.n[1], p.bc, tb, cf);
+    kern<<<grid, dim3(kBX, k2BY), smem, s>>>((const T*)in, (T*)out, p.n[0], p.n[1], p.ldx, p.bc, tb, cf);
     return cudaGetLastError();
 }
 
@@ -680,7 +683,7 @@ cudaError_t launch3d_tiles(const GatherProblem& p, const void* in, void* out, in
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((p.n[2] + k3TX - 1) / k3TX), (unsigned)((p.n[1] + k3TY - 1) / k3TY),
               (unsigned)((p.n[0] + k3TZ - 1) / k3TZ));
-    kern<<<grid, dim3(kBX, k3BY), smem, s>>>((const T*)in, (T*)out, p.n[0], p.n[1], p.n[2], p.bc, tb, cf);
+    kern<<<grid, dim3(kBX, k3BY), smem, s>>>((const T*)in, (T*)out, p.n[0], p.n[1], p.n[2], p.ldx, p.bc, tb, cf);
     return cudaGetLastError();
 }
 
@@ -701,15 +704,13 @@ int sm_count() {
 // TMA tiled view of a C-order grid: dims (innermost first) and element type;
 // false when the driver entry point is missing or the encoder rejects it.
 template <typename T>
-bool encode_grid_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims, const cuuint32_t* box) {
+bool encode_grid_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims, int64_t ldx,
+                     const cuuint32_t* box) {
     auto enc = mxu::get_encode();
     if (!enc) return false;
-    cuuint64_t strides[2];
-    cuuint64_t st = sizeof(T);
-    for (int d = 0; d + 1 < rank; ++d) {
-        st *= dims[d];
-        strides[d] = st;
-    }
+    cuuint64_t strides[2];   // rows of ldx elements; planes of dims[1] rows
+    strides[0] = (cuuint64_t)ldx * sizeof(T);
+    if (rank == 3) strides[1] = strides[0] * dims[1];
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank,
                const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -720,8 +721,7 @@ bool encode_grid_map(CUtensorMap* map, const void* base, int rank, const cuuint6
 // The TMA kernels need 16-byte aligned grid bases and rows.
 template <typename T>
 bool tma_layout_ok(const GatherProblem& p, const void* in) {
-    const int64_t nx = p.n[p.ndim - 1];
-    return ((uintptr_t)in & 15u) == 0 && (nx * (int64_t)sizeof(T)) % 16 == 0;
+    return ((uintptr_t)in & 15u) == 0 && (p.ldx * (int64_t)sizeof(T)) % 16 == 0;
 }
 
 template <typename T, int R, bool STAR>
@@ -737,6 +737,7 @@ cudaError_t launch2d(const GatherProblem& p, const void* in, void* out, int tb, 
     a.in = in;
     a.out = out;
     a.err = p.err;
+    a.ldx = p.ldx;
     a.ny = (int)p.n[0];
     a.nx = (int)p.n[1];
     a.bc = p.bc;
@@ -746,7 +747,7 @@ cudaError_t launch2d(const GatherProblem& p, const void* in, void* out, int tb, 
     alignas(64) CUtensorMap tin;
     const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny};
     const cuuint32_t box[2] = {(cuuint32_t)L.SX, (cuuint32_t)L.SY};
-    if (!encode_grid_map<T>(&tin, in, 2, dims, box)) return cudaErrorInvalidValue;
+    if (!encode_grid_map<T>(&tin, in, 2, dims, p.ldx, box)) return cudaErrorInvalidValue;
     auto kern = gather2d_tma_kernel<T, R, STAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -772,6 +773,7 @@ cudaError_t launch3d(const GatherProblem& p, const void* in, void* out, int tb, 
     a.in = in;
     a.out = out;
     a.err = p.err;
+    a.ldx = p.ldx;
     a.nz = (int)p.n[0];
     a.ny = (int)p.n[1];
     a.nx = (int)p.n[2];
@@ -783,7 +785,7 @@ cudaError_t launch3d(const GatherProblem& p, const void* in, void* out, int tb, 
     alignas(64) CUtensorMap tin;
     const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
     const cuuint32_t box[3] = {(cuuint32_t)L::SX, (cuuint32_t)L::SY, 1};
-    if (!encode_grid_map<T>(&tin, in, 3, dims, box)) return cudaErrorInvalidValue;
+    if (!encode_grid_map<T>(&tin, in, 3, dims, p.ldx, box)) return cudaErrorInvalidValue;
     auto kern = gather3d_stream_kernel<T, R, STAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

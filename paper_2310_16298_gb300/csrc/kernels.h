@@ -16,6 +16,7 @@ struct GatherProblem {
     bool f64;          // storage/compute type FP64 (else FP32)
     int bc;            // kBcDirichlet | kBcPeriodic
     const double* cg;  // host: dense C^g, (2r+1)^ndim, gather orientation
+    int64_t ldx = 0;   // row stride of the grids (elements); planes are n[ndim-2] rows
     unsigned int* err = nullptr;  // device view of the plan's host-mapped error word (bounded waits)
 };
 

@@ -148,6 +148,7 @@ struct MxArgs2D {
     unsigned int* err;         // device error word (host-mapped)
     int* sched;                // [0] next tile to hand out, [1] CTAs finished (both 0 between launches)
     int ny, nx;
+    int64_t ldx;               // row stride of the grids (elements)
     int bc, nparts;            // operand parts of the input split (1..3)
     int tiles_x, tiles_total;
     int rows_even, rows_odd;   // rows of the even / odd row-parity views
@@ -359,10 +360,15 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                     for (int c4 = 0; c4 < GW; c4 += 4) {
                         float4 v = *reinterpret_cast<const float4*>(row + kNb * j + GW * g + c4);
                         if (fix) {
+                            // element by element: with an extent that is not a
+                            // multiple of 4 the wrapped columns are neither
+                            // 16-byte aligned nor contiguous
                             const int gx = xj - kPad + GW * g + c4;
-                            if (gy < 0 || gy >= args.ny || gx < 0 || gx >= args.nx)
-                                v = *reinterpret_cast<const float4*>(args.in + wrap_index(gy, args.ny) * args.nx +
-                                                                     wrap_index(gx, args.nx));
+                            if (gy < 0 || gy >= args.ny || gx < 0 || gx + 3 >= args.nx) {
+                                const float* rp = args.in + wrap_index(gy, args.ny) * args.ldx;
+                                v = make_float4(rp[wrap_index(gx, args.nx)], rp[wrap_index(gx + 1, args.nx)],
+                                                rp[wrap_index(gx + 2, args.nx)], rp[wrap_index(gx + 3, args.nx)]);
+                            }
                         }
                         x[g][c4] = v.x;
                         x[g][c4 + 1] = v.y;
@@ -583,14 +589,15 @@ std::vector<std::array<const double*, 2>> pair_blocks(int r, const double* cg) {
     return out;
 }
 
-// Row-parity view of a row-major grid: rows parity, parity + 2, ... (a 2D
-// tensor of rows_p rows with a row stride of two grid rows).
-bool encode_parity_map(CUtensorMap* map, const float* base, int rows_p, int nx, int box_x, int box_y,
+// Row-parity view of a row-major grid with rows of ldx elements: rows parity,
+// parity + 2, ... (a 2D tensor of rows_p rows of nx elements, row stride two
+// grid rows).
+bool encode_parity_map(CUtensorMap* map, const float* base, int rows_p, int nx, int64_t ldx, int box_x, int box_y,
                        CUtensorMapSwizzle swz, CUtensorMapL2promotion l2) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows_p};
-    cuuint64_t strides[1] = {(cuuint64_t)nx * 8};
+    cuuint64_t strides[1] = {(cuuint64_t)ldx * 8};
     cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
     cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
@@ -623,8 +630,8 @@ bool mx_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2, BF16X3 or BF16_W2";
         return false;
     }
-    if (q.n[1] % 4 != 0) {
-        if (why) *why = "the contiguous extent must be a multiple of 4 (16-byte TMA rows)";
+    if (q.ldx % 4 != 0) {
+        if (why) *why = "the row stride must be a multiple of 4 (16-byte TMA rows)";
         return false;
     }
     if (q.n[0] < 2) {
@@ -642,6 +649,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     if (!mx_supported(q, why)) return STENCIL_EUNSUPPORTED;
     p->ndim = q.ndim;
     for (int d = 0; d < 3; ++d) p->n[d] = q.n[d];
+    p->ldx = q.ldx;
     p->r = q.r;
     p->bc = q.bc;
     p->prec = q.prec;
@@ -750,6 +758,7 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     a.sched = st->sched;
     a.ny = ny;
     a.nx = nx;
+    a.ldx = p.ldx;
     a.bc = p.bc;
     a.nparts = operand_parts(p.prec);
     a.nprod = products_for(p.prec);
@@ -763,13 +772,14 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     float* out = (float*)dst;
     alignas(64) CUtensorMap te, to, oe, oo;
     const int kp = raw_pitch(RWD);
-    if (!encode_parity_map(&te, in, a.rows_even, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const int64_t ld = p.ldx;
+    if (!encode_parity_map(&te, in, a.rows_even, nx, ld, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
-        !encode_parity_map(&to, in + nx, a.rows_odd, nx, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
+        !encode_parity_map(&to, in + ld, a.rows_odd, nx, ld, kp, kLanes, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
-        !encode_parity_map(&oe, out, a.rows_even, nx, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
+        !encode_parity_map(&oe, out, a.rows_even, nx, ld, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE) ||
-        !encode_parity_map(&oo, out + nx, a.rows_odd, nx, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
+        !encode_parity_map(&oo, out + ld, a.rows_odd, nx, ld, kTw, kLanes - 2 * dm, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE))
         return cudaErrorInvalidValue;
     const KernelInfo ki = kernel_for(p.r, st->bf, operand_parts(p.prec));

@@ -22,11 +22,13 @@ struct MxRequest {
     int prec = STENCIL_PREC_TF32X3;
     int tb = 0;                   // 0 = library choice
     int cover = 0;                // stencil_cover (stars only)
+    int64_t ldx = 0;              // row stride of the grids the kernels see (elements)
 };
 
 struct MxPlan {
     int ndim = 2;
     int64_t n[3] = {1, 1, 1};
+    int64_t ldx = 0;      // row stride of the grids the kernels read and write (elements)
     int r = 1;
     int bc = 0;
     int prec = STENCIL_PREC_TF32X3;

@@ -15,6 +15,10 @@
 //
 // Work unit = (32-row-slab tile in y, NB columns in x, a chunk of output
 // planes in z); the unit streams its chunk plus R halo planes on either side.
+// Boundaries: the zero Dirichlet halo is TMA's out-of-bounds fill; with a
+// periodic boundary the producer wraps the plane index (whole planes) and the
+// split warps replace the rows and columns of edge tiles that lie outside the
+// grid by their wrapped values, read from the source grid.
 // Roles per CTA as in the 2D kernel: TMA producer warp, two MMA issuer warps
 // (alternate input planes), 8 split warps (input plane -> TF32 hi/lo A
 // operand in tensor memory), 8 epilogue warps (tensor memory -> plane
@@ -90,7 +94,7 @@ __host__ __device__ constexpr int bop_bytes3(int nb, int lines, bool bf) {
 }
 __host__ __device__ constexpr int smem_fixed3(int nb, int lines, bool bf) {
     return 1024 + out_bytes3(nb) + bop_bytes3(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16) + 8 * 2 * kUnitRing +
-           4 * (kUnitRing + kMaxRawStages + 8);
+           4 * (kUnitRing + 2 * kMaxRawStages + 8);
 }
 __host__ __device__ constexpr int raw_stages3(int nb, int lines, bool bf) {
     return (kSmemBudget - smem_fixed3(nb, lines, bf)) / raw_stage_bytes3(raw_pitch3(window3(nb, bf))) < kMaxRawStages
@@ -102,10 +106,13 @@ __host__ __device__ constexpr int smem_bytes_3d(int nb, int lines, bool bf) {
 }
 
 struct MxArgs3D {
+    const float* in;      // source grid (periodic halo fix-up reads it directly)
+    int bc;
     const void* bops;     // banded operands [part][kchunk][line*NB + q][16 bytes]
     unsigned int* err;    // device error word (host-mapped)
     int* sched;           // [0] next unit to hand out, [1] CTAs finished (both 0 between launches)
     int nz, ny, nx;
+    int64_t ldx;          // row stride of the grids (elements); planes are ny rows
     int nparts;           // operand parts of the input split (1..3)
     int tiles_x, tiles_y, chunks, units;
     uint32_t bop_bytes;
@@ -166,6 +173,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     volatile int* unit_ring = abort_flag + 1;               // [kUnitRing] unit ids (-1: no more units)
     volatile int* stage_unit = unit_ring + kUnitRing;       // [kRawStages] unit of each input plane stage
     volatile int* a_unit = stage_unit + kMaxRawStages;      // [AST] -1 marks the end for the MMA issuers
+    volatile int* stage_z = a_unit + 8;                     // [kRawStages] grid plane of each input stage
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -240,12 +248,15 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
+                    int gz = Z0 - R + iz;
+                    if (args.bc == kBcPeriodic) gz = (int)wrap_index(gz, args.nz);
                     stage_unit[s] = u;
+                    stage_z[s] = gz;
                     unsigned char* dst = raw + s * RSB;
                     ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
 #pragma unroll
                     for (int q = 0; q < kQuarters; ++q)
-                        ptx::tma_load_3d(dst + q * SLAB_BOX, &tmap, X0 - kPad, Y0 + q * ROWS_OUT - R, Z0 - R + iz,
+                        ptx::tma_load_3d(dst + q * SLAB_BOX, &tmap, X0 - kPad, Y0 + q * ROWS_OUT - R, gz,
                                          &full[s]);
                     issued = i + 1;
                 }
@@ -308,6 +319,17 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     ptx::tc_fence_after();
                     const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
                     const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
+                    // periodic boundary: rows and columns of an edge tile outside
+                    // the grid are read wrapped from the source plane
+                    int ux = 0, gy = 0, gz = 0;
+                    bool fix = false;
+                    if (args.bc == kBcPeriodic) {
+                        int uy, uz;
+                        unit_origin(stage_unit[rs], ux, uy, uz);
+                        gy = uy + q * ROWS_OUT - R + lane;
+                        gz = stage_z[rs];
+                        fix = gy < 0 || gy >= args.ny || ux - kPad < 0 || ux - kPad + K > args.nx;
+                    }
 #pragma unroll
                     for (int g0 = 0; g0 < NG; g0 += kSubs) {
                         const int g = g0 + sub;
@@ -316,7 +338,19 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         float x[GW];
 #pragma unroll
                         for (int c4 = 0; c4 < GW; c4 += 4) {
-                            const float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
+                            float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
+                            if (fix) {
+                                // element by element: with an extent that is not a
+                                // multiple of 4 the wrapped columns are neither
+                                // 16-byte aligned nor contiguous
+                                const int gx = ux - kPad + c0 + c4;
+                                if (gy < 0 || gy >= args.ny || gx < 0 || gx + 3 >= args.nx) {
+                                    const float* rp =
+                                        args.in + ((int64_t)gz * args.ny + wrap_index(gy, args.ny)) * args.ldx;
+                                    v = make_float4(rp[wrap_index(gx, args.nx)], rp[wrap_index(gx + 1, args.nx)],
+                                                    rp[wrap_index(gx + 2, args.nx)], rp[wrap_index(gx + 3, args.nx)]);
+                                }
+                            }
                             x[c4] = v.x;
                             x[c4 + 1] = v.y;
                             x[c4 + 2] = v.z;
@@ -541,11 +575,11 @@ int line3_b(int r, bool star, int l) {
     return star ? (l < r || l >= r + W ? r : l - r) : l % W;
 }
 
-bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int nx, int pitch) {
+bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int nx, int64_t ldx, int pitch) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)ldx * 4, (cuuint64_t)ldx * ny * 4};
     cuuint32_t box[3] = {(cuuint32_t)pitch, (cuuint32_t)kSlabRows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
@@ -554,11 +588,11 @@ bool encode_in_map_3d(CUtensorMap* map, const float* base, int nz, int ny, int n
 }
 
 // One box = one epilogue warp's share of an output plane tile (cols = NB/2).
-bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, int cols, int rows) {
+bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, int64_t ldx, int cols, int rows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)ldx * 4, (cuuint64_t)ldx * ny * 4};
     cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
@@ -591,10 +625,6 @@ bool mx3d_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "the outer-product kernels run TF32, TF32X3, BF16, BF16X2, BF16X3 or BF16_W2";
         return false;
     }
-    if (q.bc != kBcDirichlet) {
-        if (why) *why = "the 3D matrixized kernel handles the zero Dirichlet boundary only";
-        return false;
-    }
     if (q.cover == STENCIL_COVER_HYBRID && !q.star) {
         if (why) *why = "the hybrid line cover applies to star stencils";
         return false;
@@ -603,8 +633,8 @@ bool mx3d_supported(const MxRequest& q, std::string* why) {
         if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27-point box";
         return false;
     }
-    if (q.n[2] % 4 != 0) {
-        if (why) *why = "the contiguous extent must be a multiple of 4 (16-byte TMA rows)";
+    if (q.ldx % 4 != 0) {
+        if (why) *why = "the row stride must be a multiple of 4 (16-byte TMA rows)";
         return false;
     }
     if (q.tb > 1) {
@@ -706,12 +736,15 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     const int rows_tile = kQuarters * (kSlabRows - 2 * p.r);
     MxArgs3D a;
     memset(&a, 0, sizeof(a));
+    a.in = (const float*)src;
+    a.bc = p.bc;
     a.bops = p.d_operands;
     a.err = st->err_dev;
     a.sched = st->sched;
     a.nz = nz;
     a.ny = ny;
     a.nx = nx;
+    a.ldx = p.ldx;
     a.nparts = operand_parts(p.prec);
     a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;
@@ -721,8 +754,8 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     a.units = a.tiles_x * a.tiles_y * a.chunks;
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map, map_out;
-    if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, raw_pitch3(in_w))) return cudaErrorInvalidValue;
-    if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, st->nb / kSubs, kSlabRows - 2 * p.r))
+    if (!encode_in_map_3d(&map, (const float*)src, nz, ny, nx, p.ldx, raw_pitch3(in_w))) return cudaErrorInvalidValue;
+    if (!encode_out_map_3d(&map_out, (float*)dst, nz, ny, nx, p.ldx, st->nb / kSubs, kSlabRows - 2 * p.r))
         return cudaErrorInvalidValue;
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
     for (int k = 0; k < 12; ++k) a.sw[k] = st->sw[k];

@@ -29,6 +29,12 @@ struct stencil_plan_s {
     int64_t points = 0;
     size_t grid_bytes = 0;
     void* scratch = nullptr;
+    int64_t pitch = 0;              // row stride of the caller's grids (elements)
+    int64_t ldx = 0;                // row stride of the grids the kernels see (elements)
+    bool repack = false;            // caller rows are not 16-byte multiples: the kernels run on
+                                    // padded copies (pad, scratch) of row stride ldx
+    void* pad = nullptr;            // first padded grid (repack only)
+    size_t pad_bytes = 0;           // bytes of one padded grid
     cudaStream_t stream = nullptr;  // for stencil_submit
     stx::MxPlan* mx = nullptr;
     uint64_t id = 0;                // unique per plan (tickets refer to plans by id)

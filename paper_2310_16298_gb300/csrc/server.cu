@@ -326,7 +326,10 @@ extern "C" stencil_status stencil_server_submit(stencil_server_t S, const stenci
     q->hi = rq->hi;
     q->steps = rq->steps;
     q->grid_bytes = (size_t)pts * dtype_size(rq->dtype);
-    q->charge = 2 * q->grid_bytes + (1 << 20);  // the request's grid, the plan's scratch grid, operands
+    // the request's grid, the plan's scratch grid, operands; plus a padded grid
+    // when rows are not 16-byte multiples (the plan repacks for the tensor cores)
+    q->charge = 2 * q->grid_bytes + (1 << 20);
+    if ((q->shape[q->ndim - 1] * (int64_t)dtype_size(q->dtype)) % 16 != 0) q->charge += q->grid_bytes + (q->grid_bytes >> 2);
     if ((int64_t)q->charge > S->budget) return fail(STENCIL_ENOMEM, "request larger than the whole budget");
     std::lock_guard<std::mutex> lk(S->mu);
     q->id = S->next_id++;

@@ -74,16 +74,17 @@ def test_mx_2d_4096_ragged_many_tiles_per_cta():
     ("box", "auto", "tf32x3"),
     ("box", "auto", "bf16x3"),
 ])
-def test_mx_3d_more_units_than_sms(kind, cover, prec):
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_mx_3d_more_units_than_sms(kind, cover, prec, bc):
     """192 x 480 x 256, r = 1: 6 chunks of 32 planes x 4 y tiles x (8 or 16)
     x tiles = 192 or 384 work units, more than the SMs."""
     shape, r, steps = (192, 480, 256), 1, 3
     a, cg = problem(shape, r, kind, 30, lo=-1.0, hi=1.0)
-    got, info = run(a, r, kind, cg, "f32", "dirichlet", steps, impl="matrixized", prec=prec, cover=cover)
+    got, info = run(a, r, kind, cg, "f32", bc, steps, impl="matrixized", prec=prec, cover=cover)
     assert info["impl"] == 2
     units = 6 * 4 * (256 // info["tile_n"])
     assert units > num_sms()
-    check(got, oracle.gather(a, r, cg, "dirichlet", steps), TOL[prec], f"3d {kind} {cover} {prec}")
+    check(got, oracle.gather(a, r, cg, bc, steps), TOL[prec], f"3d {kind} {cover} {prec} {bc}")
 
 
 def workload_problem(shape, r, kind, lo):

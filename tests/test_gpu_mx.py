@@ -77,11 +77,16 @@ def test_mx_in_place_and_zero_steps():
     assert np.array_equal(got, a)
 
 
-def test_mx_rejects_unaligned_rows():
+def test_mx_takes_unaligned_rows_through_padded_grids():
+    """Rows that are not 16-byte multiples run on the tensor-core kernel
+    through the plan's padded grids (two of them, reported as scratch)."""
     import paper_2310_16298_gb300 as sx
-    with pytest.raises(sx.StencilError) as ei:
-        sx.stencil_plan_create((64, 66), 1, "box", np.ones((3, 3)) / 9, "f32", sx.make_options(impl="matrixized"))
-    assert ei.value.status == sx.EUNSUPPORTED
+    plan = sx.stencil_plan_create((64, 66), 1, "box", np.ones((3, 3)) / 9, "f32", sx.make_options(impl="matrixized"))
+    try:
+        info = sx.stencil_plan_info(plan)
+        assert info["impl"] == 2 and info["scratch_bytes"] >= 2 * 64 * 68 * 4
+    finally:
+        sx.stencil_plan_destroy(plan)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16", "bf16w2"])
@@ -195,3 +200,16 @@ def test_arbitrary_weight_patterns(pattern, impl):
     a = si.round_to(si.field_uniform((300, 196), 77, -1.0, 1.0), "f32")
     got, info = run(a, r, "box", cg, "f32", "periodic", 4, impl=impl, prec="tf32x3" if impl == "matrixized" else "native")
     check(got, oracle.gather(a, r, cg, "periodic", 4), 1e-5, f"{pattern} {impl}")
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("kind,r,cover", [("star", 1, "hybrid"), ("star", 1, "parallel"), ("box", 1, "auto"),
+                                          ("star", 2, "hybrid"), ("star", 3, "parallel")])
+@pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
+def test_mx_3d_periodic(prec, kind, r, cover, shape):
+    """Periodic 3D sweeps: wrapped plane indices and wrapped halo rows and
+    columns of the edge tiles (several y and x tiles, ragged tails)."""
+    a, cg = problem(3, shape, r, kind, seed=80 + r)
+    got, info = run(a, r, kind, cg, "f32", "periodic", 3, impl="matrixized", prec=prec, cover=cover)
+    assert info["impl"] == 2
+    check(got, oracle.gather(a, r, cg, "periodic", 3), TOL[prec], f"mx 3d periodic {kind} r={r} {cover} {prec}")
