@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
                     choices=["box25-8192", "star7-512", "box27-512", "sine7-512", "sine27-512", "jacobi-256",
-                             "batch-1024", "serve-2000", "error-growth", "cover-study"])
+                             "batch-1024", "serve-2000", "error-growth", "cover-study", "ablation"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
     ap.add_argument("--tsteps", type=int, default=0, help="stencil time steps per solve (0 = the workload's own)")
@@ -467,6 +467,51 @@ def run_cover_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation(args):
+    """Scheduling ablation of the 3D matrixized kernel (the unrolling study of
+    the paper's Sec. 4.2 on this GPU): one sweep of the 7-point star (hybrid
+    cover) and of the 27-point box, 512^3 FP32 TF32x3, for work units of
+    1 .. 128 output planes.  A unit streams its planes plus 2r halo planes,
+    so deeper units re-read fewer planes (operand reuse across planes) but
+    leave fewer units to balance across the SMs."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_2310_16298_gb300 as sx
+    import stencil_inputs as si
+    torch.cuda.set_device(local)
+    side = args.side or 512
+    shape = (side, side, side)
+    x = torch.rand(shape, device="cuda") * 2 - 1
+    y = torch.empty_like(x)
+    stream = torch.cuda.Stream()
+    rows = []
+    for kind in ("star", "box"):
+        cg = si.coeffs_random(3, 1, kind, 103, dtype="f32")
+        for up in (1, 2, 4, 8, 16, 32, 64, 128):
+            plan = sx.Plan(shape, 1, kind, cg, "f32", bc="dirichlet", impl="matrixized", prec="tf32x3",
+                           cover="hybrid" if kind == "star" else "auto", unit_planes=up)
+            for _ in range(2):
+                plan.apply(x, y, 1, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for a_, b_ in ev:
+                a_.record(stream)
+                plan.apply(x, y, 1, stream)
+                b_.record(stream)
+            stream.synchronize()
+            ms = float(np.median([a_.elapsed_time(b_) for a_, b_ in ev]))
+            tile_n = plan.info["tile_n"]
+            units = -(-side // up) * -(-side // 120) * -(-side // tile_n)
+            rows.append({"kind": kind, "unit_planes": up, "input_planes_per_output_plane": (up + 2) / up,
+                         "units": units, "ms_per_sweep": ms, "gstencil_s": x.numel() / ms / 1e6})
+            plan.close()
+    line = {"metric": "scheduling ablation: GStencil/s of one 3D sweep per work-unit depth", "value": None,
+            "unit": "GStencil/s", "workload": f"3D r=1 {side}^3 FP32 TF32x3, zero Dirichlet, matrixized kernel",
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving_workload(args):
     """Poisson arrivals of mixed stencil solves (70% 2D 128^2..4096^2 r=1..3
     star|box, 30% 3D 64^3..384^3 7/27-point, 10% FP64, steps 10..500) served
@@ -563,6 +608,8 @@ def main():
         return run_error_growth(args)
     if args.workload == "cover-study":
         return run_cover_study(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_16298_gb300 as sx

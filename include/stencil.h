@@ -114,7 +114,11 @@ typedef struct {
                          elements are neither read nor written.  Packed grids whose rows are
                          not 16-byte multiples run on the tensor-core kernels through two
                          padded grids the plan owns (one strided copy in, one out per apply) */
-    int32_t reserved[2];
+    int32_t unit_planes; /* 3D matrixized kernel: output planes per work unit, 1..1024 (0 = the
+                         library's 32).  Each unit streams its planes plus 2r halo planes, so
+                         the depth trades re-read halo planes against the number of units
+                         (load balance); exposed for the scheduling ablation          */
+    int32_t reserved[1];
 } stencil_options;
 
 /* Plan introspection (filled by stencil_plan_info). */

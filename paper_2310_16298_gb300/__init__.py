@@ -48,7 +48,7 @@ class StencilError(RuntimeError):
 class stencil_options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("bc", ctypes.c_int32), ("impl", ctypes.c_int32),
                 ("tb", ctypes.c_int32), ("cover", ctypes.c_int32), ("pitch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("unit_planes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class stencil_batch_info_t(ctypes.Structure):
@@ -174,7 +174,8 @@ def stencil_version() -> str:
 COVERS = {"auto": 0, "parallel": 1, "hybrid": 2}
 
 
-def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto", pitch=0) -> stencil_options:
+def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto", pitch=0,
+                 unit_planes=0) -> stencil_options:
     o = stencil_options()
     o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     o.bc = BCS[bc] if isinstance(bc, str) else int(bc)
@@ -182,6 +183,7 @@ def make_options(prec="native", bc="dirichlet", impl="auto", tb=0, cover="auto",
     o.tb = int(tb)
     o.cover = COVERS[cover] if isinstance(cover, str) else int(cover)
     o.pitch = int(pitch)
+    o.unit_planes = int(unit_planes)
     return o
 
 
@@ -403,11 +405,11 @@ class Plan:
     """A plan for torch CUDA tensors of the plan's dtype and shape."""
 
     def __init__(self, shape, radius, kind, coeffs, dtype="f32", bc="dirichlet", impl="auto",
-                 prec="native", tb=0, cover="auto"):
+                 prec="native", tb=0, cover="auto", pitch=0, unit_planes=0):
         self.shape = tuple(int(s) for s in shape)
         self.dtype = dtype
         self.handle = stencil_plan_create(self.shape, radius, kind, coeffs, dtype,
-                                          make_options(prec, bc, impl, tb, cover))
+                                          make_options(prec, bc, impl, tb, cover, pitch, unit_planes))
         self.info = stencil_plan_info(self.handle)
 
     def apply(self, x, out=None, steps=1, stream=None):

@@ -319,6 +319,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
         return fail(STENCIL_EINVAL, "cover out of range");
     const int64_t es = (dtype == STENCIL_F64) ? 8 : 4;
     if (o.pitch < 0) return fail(STENCIL_EINVAL, "pitch must be >= 0");
+    if (o.unit_planes < 0 || o.unit_planes > 1024) return fail(STENCIL_EINVAL, "unit_planes must be in 0..1024");
     if (o.pitch > 0 && (o.pitch < shape[ndim - 1] || (o.pitch * es) % 16 != 0))
         return fail(STENCIL_EINVAL, "pitch must be at least the contiguous extent and give 16-byte rows");
     const int W = 2 * radius + 1;
@@ -377,6 +378,7 @@ extern "C" stencil_status stencil_plan_create(stencil_plan_t* out, int ndim, con
     req.cg = p->cg.data();
     req.prec = (prec == STENCIL_PREC_NATIVE) ? STENCIL_PREC_TF32X3 : prec;
     req.tb = o.tb;
+    req.unit_planes = o.unit_planes;
     // The tensor-core kernels stage rows with TMA, which needs 16-byte rows:
     // packed grids whose rows are not run on padded copies the plan owns.
     const bool aligned_rows = (p->pitch * es) % 16 == 0;

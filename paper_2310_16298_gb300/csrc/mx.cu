@@ -650,6 +650,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->ndim = q.ndim;
     for (int d = 0; d < 3; ++d) p->n[d] = q.n[d];
     p->ldx = q.ldx;
+    p->unit_planes = q.unit_planes;
     p->r = q.r;
     p->bc = q.bc;
     p->prec = q.prec;

@@ -23,6 +23,7 @@ struct MxRequest {
     int tb = 0;                   // 0 = library choice
     int cover = 0;                // stencil_cover (stars only)
     int64_t ldx = 0;              // row stride of the grids the kernels see (elements)
+    int unit_planes = 0;          // 3D: output planes per work unit (0 = library choice)
 };
 
 struct MxPlan {
@@ -37,6 +38,7 @@ struct MxPlan {
     int n_lines = 0;      // lines on the tensor cores
     int n_scalar = 0;     // weights applied on CUDA cores
     int cover = STENCIL_COVER_PARALLEL;   // line cover the plan runs
+    int unit_planes = 0;  // 3D: output planes per work unit (0 = library choice)
     size_t operand_bytes = 0;
     void* d_operands = nullptr;  // banded line operands (device), kernel-specific layout
     void* d_scalars = nullptr;   // scalar-term table (device)

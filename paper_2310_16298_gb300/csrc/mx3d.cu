@@ -53,7 +53,7 @@ constexpr int kMaxRawStages = 6;
 constexpr int kUnitRing = 8;                // unit ids handed from the producer to the epilogue
 constexpr int kTmemCols = 512;
 constexpr int kSmemBudget = 227 * 1024;
-constexpr int kChunk = 32;  // output planes per work unit
+constexpr int kChunk = 32;  // output planes per work unit (library choice; plans may set their own)
 
 // Coefficient lines of a 3D stencil: (a = z offset, b = y offset) pairs that
 // carry weights.  Box: all (2R+1)^2 pairs.  Star, parallel cover: (a, R) for
@@ -115,6 +115,7 @@ struct MxArgs3D {
     int64_t ldx;          // row stride of the grids (elements); planes are ny rows
     int nparts;           // operand parts of the input split (1..3)
     int tiles_x, tiles_y, chunks, units;
+    int chunk;            // output planes per work unit
     uint32_t bop_bytes;
     uint32_t bpart_bytes;
     int nprod;
@@ -142,7 +143,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     constexpr int RSB = raw_stage_bytes3(KP);
     constexpr int kRawStages = raw_stages3(NB, L, BF);
     constexpr int OWB = out_warp_bytes3(NB);
-    constexpr int PLANES = kChunk + 2 * R;  // input planes per work unit
+    const int PLANES = args.chunk + 2 * R;  // input planes per work unit
     constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
     static_assert(kRawStages >= 3, "TMA ring too shallow");
     static_assert(N <= 256 && N % 16 == 0, "MMA N");
@@ -215,7 +216,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     auto unit_origin = [&](int u, int& X0, int& Y0, int& Z0) {
         X0 = (u % args.tiles_x) * NB;
         Y0 = ((u / args.tiles_x) % args.tiles_y) * (kQuarters * ROWS_OUT);
-        Z0 = (u / (args.tiles_x * args.tiles_y)) * kChunk;
+        Z0 = (u / (args.tiles_x * args.tiles_y)) * args.chunk;
     };
 
     if (warp == 0) {
@@ -750,7 +751,8 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     a.bpart_bytes = st->bpart_bytes;
     a.tiles_x = (nx + st->nb - 1) / st->nb;
     a.tiles_y = (ny + rows_tile - 1) / rows_tile;
-    a.chunks = (nz + kChunk - 1) / kChunk;
+    a.chunk = p.unit_planes > 0 ? p.unit_planes : kChunk;
+    a.chunks = (nz + a.chunk - 1) / a.chunk;
     a.units = a.tiles_x * a.tiles_y * a.chunks;
     a.bop_bytes = st->bop_bytes;
     alignas(64) CUtensorMap map, map_out;
