@@ -133,6 +133,11 @@ typedef struct {
     int32_t device_error; /* error bits: nonzero once a kernel of the plan gave up a
                              bounded wait (or stencil_plan_raise_error set bits)        */
     int32_t cover;        /* stencil_cover the matrixized kernel runs (0 for GATHER)    */
+    int32_t kernels_per_sweep; /* kernel launches per sweep: 2 for MATRIXIZED plans with
+                             a periodic boundary (the tensor-core kernel, whose TMA
+                             loads see zeros outside the grid in x and y, then a
+                             kernel over the boundary strips that adds the wrapped
+                             terms), else 1                                             */
 } stencil_plan_info_t;
 
 /* ---------------------------------------------------------------------------

@@ -78,7 +78,7 @@ class stencil_plan_info_t(ctypes.Structure):
     _fields_ = [("impl", ctypes.c_int32), ("prec", ctypes.c_int32), ("tb", ctypes.c_int32),
                 ("n_lines", ctypes.c_int32), ("n_scalar", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("device_error", ctypes.c_int32),
-                ("cover", ctypes.c_int32)]
+                ("cover", ctypes.c_int32), ("kernels_per_sweep", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -465,6 +465,7 @@ extern "C" stencil_status stencil_plan_info(stencil_plan_t p, stencil_plan_info_
         info->tile_n = p->mx->nb;
         info->cover = p->mx->cover;
     }
+    info->kernels_per_sweep = p->mx && p->mx->n_edge_terms > 0 ? 2 : 1;
     info->device_error = (int32_t)plan_error_bits(p);
     return STENCIL_OK;
 }

@@ -32,6 +32,10 @@
 // Tiles are handed out at run time (an atomic counter per plan, reset by the
 // last CTA to finish), so SMs that run faster take more tiles.
 //
+// Boundaries: rows and columns outside the grid are TMA's out-of-bounds zero
+// fill (the zero Dirichlet halo); with a periodic boundary the terms that
+// wrap are added afterwards by the edge kernel (edges.cu).
+//
 // Roles (one persistent CTA per SM, warp specialised):
 //  * warp 0: TMA producer.  A tile is 4 lane quarters x 64 input rows; each
 //    quarter is loaded as two 32-row boxes through row-parity tensor maps
@@ -143,13 +147,12 @@ __host__ __device__ constexpr int smem_bytes() {
 }
 
 struct MxArgs2D {
-    const float* in;           // source grid (periodic halo fix-up reads it directly)
     const void* bops;          // block operands [part][kchunk][block*16 + q][16 bytes]
     unsigned int* err;         // device error word (host-mapped)
     int* sched;                // [0] next tile to hand out, [1] CTAs finished (both 0 between launches)
     int ny, nx;
     int64_t ldx;               // row stride of the grids (elements)
-    int bc, nparts;            // operand parts of the input split (1..3)
+    int nparts;                // operand parts of the input split (1..3)
     int tiles_x, tiles_total;
     int rows_even, rows_odd;   // rows of the even / odd row-parity views
     uint32_t bop_bytes;        // every part
@@ -184,7 +187,6 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
     constexpr int A_COLS = NP * PC;         // NP operand parts (1..3) per A stage
     constexpr int GW = F::kGroup;           // input columns per split group
     constexpr int NG = W / GW;              // split groups per row
-    constexpr int WU = kNb + 2 * kPad;      // window columns that carry weights
     constexpr int KP = raw_pitch(raw_row<BF>(kNb));
     constexpr int SLAB = kLanes * KP * 4;   // one (parity, quarter) box
     constexpr int RSB = raw_stage_bytes<BF>();
@@ -342,34 +344,17 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
                 }
                 break;
             }
-            const int X0 = (t % args.tiles_x) * kTw;
-            const int Y0 = (t / args.tiles_x) * (kQuarters * G::ROWS_OUT);
-            const int gy = Y0 + q * G::ROWS_OUT - 2 * G::DM + 2 * lane + e;   // input row of this thread
             const float* row =
                 reinterpret_cast<const float*>(raw + rs * RSB + (e * kQuarters + q) * SLAB) + (size_t)lane * KP;
             for (int j = 0; j < kItems; ++j, ++i) {
                 const int sa = i % AST;
                 const uint32_t pa = (uint32_t)(i / AST) & 1u;
-                const int xj = X0 + kNb * j;             // first output column of the item
-                const bool fix = (args.bc == kBcPeriodic) &&
-                                 (gy < 0 || gy >= args.ny || xj - kPad < 0 || xj - kPad + WU > args.nx);
                 float x[NG][GW];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
 #pragma unroll
                     for (int c4 = 0; c4 < GW; c4 += 4) {
-                        float4 v = *reinterpret_cast<const float4*>(row + kNb * j + GW * g + c4);
-                        if (fix) {
-                            // element by element: with an extent that is not a
-                            // multiple of 4 the wrapped columns are neither
-                            // 16-byte aligned nor contiguous
-                            const int gx = xj - kPad + GW * g + c4;
-                            if (gy < 0 || gy >= args.ny || gx < 0 || gx + 3 >= args.nx) {
-                                const float* rp = args.in + wrap_index(gy, args.ny) * args.ldx;
-                                v = make_float4(rp[wrap_index(gx, args.nx)], rp[wrap_index(gx + 1, args.nx)],
-                                                rp[wrap_index(gx + 2, args.nx)], rp[wrap_index(gx + 3, args.nx)]);
-                            }
-                        }
+                        const float4 v = *reinterpret_cast<const float4*>(row + kNb * j + GW * g + c4);
                         x[g][c4] = v.x;
                         x[g][c4 + 1] = v.y;
                         x[g][c4 + 2] = v.z;
@@ -645,6 +630,17 @@ bool mx_supported(const MxRequest& q, std::string* why) {
     return true;
 }
 
+// Periodic plans also get the boundary-term table of the edge kernel; a plan
+// that cannot get it is freed.
+static stencil_status with_edges(const MxRequest& q, MxPlan* p, std::string* why) {
+    const stencil_status s = mx_edges_build(q, p);
+    if (s != STENCIL_OK) {
+        mx_plan_free(p);
+        if (why) *why = "the periodic boundary-term table holds r <= 4 and at most 80 terms";
+    }
+    return s;
+}
+
 stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     if (!mx_supported(q, why)) return STENCIL_EUNSUPPORTED;
     p->ndim = q.ndim;
@@ -655,7 +651,11 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
     p->bc = q.bc;
     p->prec = q.prec;
     p->tb = 1;
-    if (q.ndim == 3) return mx3d_plan_build(q, p, why);
+    p->n_edge_terms = 0;
+    if (q.ndim == 3) {
+        const stencil_status s3 = mx3d_plan_build(q, p, why);
+        return s3 == STENCIL_OK ? with_edges(q, p, why) : s3;
+    }
     const bool bf = is_bf16(q.prec);
     const int W = bf ? window<true>(kNb) : window<false>(kNb);
     p->nb = kNb;
@@ -717,7 +717,7 @@ stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why) {
         if (why) *why = std::string("kernel set-up: ") + cudaGetErrorString(e);
         return STENCIL_ECUDA;
     }
-    return STENCIL_OK;
+    return with_edges(q, p, why);
 }
 
 void mx_plan_free(MxPlan* p) {
@@ -743,7 +743,12 @@ unsigned int mx_device_error(const MxPlan& p) {
 }
 
 cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s) {
-    if (p.ndim == 3) return mx3d_sweep(p, src, dst, tb, s);
+    const cudaError_t e = p.ndim == 3 ? mx3d_sweep(p, src, dst, tb, s) : mx2d_sweep(p, src, dst, tb, s);
+    // periodic boundary: the kernels ran with a zero halo in x and y
+    return e == cudaSuccess ? mx_periodic_edges(p, src, dst, s) : e;
+}
+
+cudaError_t mx2d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s) {
     if (tb != 1) return cudaErrorInvalidValue;
     if (((uintptr_t)src & 15u) || ((uintptr_t)dst & 15u)) return cudaErrorMisalignedAddress;
     const MxState* st = (const MxState*)p.tmap_storage;
@@ -753,14 +758,12 @@ cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaSt
     const int RWD = st->bf ? raw_row<true>(kNb) : raw_row<false>(kNb);
     MxArgs2D a;
     memset(&a, 0, sizeof(a));
-    a.in = (const float*)src;
     a.bops = p.d_operands;
     a.err = st->err_dev;
     a.sched = st->sched;
     a.ny = ny;
     a.nx = nx;
     a.ldx = p.ldx;
-    a.bc = p.bc;
     a.nparts = operand_parts(p.prec);
     a.nprod = products_for(p.prec);
     a.bpart_bytes = st->bpart_bytes;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/stencil.h"
 
@@ -43,6 +44,8 @@ struct MxPlan {
     void* d_operands = nullptr;  // banded line operands (device), kernel-specific layout
     void* d_scalars = nullptr;   // scalar-term table (device)
     void* tmap_storage = nullptr;
+    int n_edge_terms = 0;                    // periodic boundary terms of the edge kernel
+    std::vector<unsigned char> edge_table;   // its parameter block (edges.cu)
 };
 
 bool mx_supported(const MxRequest& q, std::string* why);
@@ -54,6 +57,14 @@ void mx3d_plan_free(MxPlan* p);
 cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
 unsigned int mx3d_device_error(const MxPlan& p);
 stencil_status mx_plan_build(const MxRequest& q, MxPlan* p, std::string* why);
+cudaError_t mx2d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
+
+// Periodic boundary (edges.cu): the tensor-core kernels see a zero halo in x
+// and y; mx_periodic_edges adds the wrapped terms of the points within r of an
+// x or y face to dst (a no-op for other plans).  mx_edges_build makes the
+// table of nonzero weights with a nonzero y or x offset that it passes.
+stencil_status mx_edges_build(const MxRequest& q, MxPlan* p);
+cudaError_t mx_periodic_edges(const MxPlan& p, const void* src, void* dst, cudaStream_t s);
 void mx_plan_free(MxPlan* p);
 cudaError_t mx_sweep(const MxPlan& p, const void* src, void* dst, int tb, cudaStream_t s);
 // Nonzero when a kernel of this plan gave up a bounded wait (bit 0: operand

@@ -16,9 +16,9 @@
 // Work unit = (32-row-slab tile in y, NB columns in x, a chunk of output
 // planes in z); the unit streams its chunk plus R halo planes on either side.
 // Boundaries: the zero Dirichlet halo is TMA's out-of-bounds fill; with a
-// periodic boundary the producer wraps the plane index (whole planes) and the
-// split warps replace the rows and columns of edge tiles that lie outside the
-// grid by their wrapped values, read from the source grid.
+// periodic boundary the producer wraps the plane index (whole planes), and the
+// terms that wrap in x or y are added afterwards by the edge kernel
+// (edges.cu) over the boundary strips.
 // Roles per CTA as in the 2D kernel: TMA producer warp, two MMA issuer warps
 // (alternate input planes), 8 split warps (input plane -> TF32 hi/lo A
 // operand in tensor memory), 8 epilogue warps (tensor memory -> plane
@@ -94,7 +94,7 @@ __host__ __device__ constexpr int bop_bytes3(int nb, int lines, bool bf) {
 }
 __host__ __device__ constexpr int smem_fixed3(int nb, int lines, bool bf) {
     return 1024 + out_bytes3(nb) + bop_bytes3(nb, lines, bf) + 8 * (2 * kMaxRawStages + 16) + 8 * 2 * kUnitRing +
-           4 * (kUnitRing + 2 * kMaxRawStages + 8);
+           4 * (kUnitRing + kMaxRawStages + 8);
 }
 __host__ __device__ constexpr int raw_stages3(int nb, int lines, bool bf) {
     return (kSmemBudget - smem_fixed3(nb, lines, bf)) / raw_stage_bytes3(raw_pitch3(window3(nb, bf))) < kMaxRawStages
@@ -106,8 +106,7 @@ __host__ __device__ constexpr int smem_bytes_3d(int nb, int lines, bool bf) {
 }
 
 struct MxArgs3D {
-    const float* in;      // source grid (periodic halo fix-up reads it directly)
-    int bc;
+    int bc;               // periodic: input planes wrap in z (x and y: edges.cu)
     const void* bops;     // banded operands [part][kchunk][line*NB + q][16 bytes]
     unsigned int* err;    // device error word (host-mapped)
     int* sched;           // [0] next unit to hand out, [1] CTAs finished (both 0 between launches)
@@ -174,7 +173,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     volatile int* unit_ring = abort_flag + 1;               // [kUnitRing] unit ids (-1: no more units)
     volatile int* stage_unit = unit_ring + kUnitRing;       // [kRawStages] unit of each input plane stage
     volatile int* a_unit = stage_unit + kMaxRawStages;      // [AST] -1 marks the end for the MMA issuers
-    volatile int* stage_z = a_unit + 8;                     // [kRawStages] grid plane of each input stage
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -252,7 +250,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     int gz = Z0 - R + iz;
                     if (args.bc == kBcPeriodic) gz = (int)wrap_index(gz, args.nz);
                     stage_unit[s] = u;
-                    stage_z[s] = gz;
                     unsigned char* dst = raw + s * RSB;
                     ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)kQuarters * SLAB_BOX);
 #pragma unroll
@@ -320,17 +317,6 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                     ptx::tc_fence_after();
                     const float* row = reinterpret_cast<const float*>(raw + rs * RSB) + (size_t)(q * kSlabRows + lane) * KP;
                     const uint32_t abase = tmem_a + lane_off + (uint32_t)(sa * A_COLS);
-                    // periodic boundary: rows and columns of an edge tile outside
-                    // the grid are read wrapped from the source plane
-                    int ux = 0, gy = 0, gz = 0;
-                    bool fix = false;
-                    if (args.bc == kBcPeriodic) {
-                        int uy, uz;
-                        unit_origin(stage_unit[rs], ux, uy, uz);
-                        gy = uy + q * ROWS_OUT - R + lane;
-                        gz = stage_z[rs];
-                        fix = gy < 0 || gy >= args.ny || ux - kPad < 0 || ux - kPad + K > args.nx;
-                    }
 #pragma unroll
                     for (int g0 = 0; g0 < NG; g0 += kSubs) {
                         const int g = g0 + sub;
@@ -339,19 +325,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         float x[GW];
 #pragma unroll
                         for (int c4 = 0; c4 < GW; c4 += 4) {
-                            float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
-                            if (fix) {
-                                // element by element: with an extent that is not a
-                                // multiple of 4 the wrapped columns are neither
-                                // 16-byte aligned nor contiguous
-                                const int gx = ux - kPad + c0 + c4;
-                                if (gy < 0 || gy >= args.ny || gx < 0 || gx + 3 >= args.nx) {
-                                    const float* rp =
-                                        args.in + ((int64_t)gz * args.ny + wrap_index(gy, args.ny)) * args.ldx;
-                                    v = make_float4(rp[wrap_index(gx, args.nx)], rp[wrap_index(gx + 1, args.nx)],
-                                                    rp[wrap_index(gx + 2, args.nx)], rp[wrap_index(gx + 3, args.nx)]);
-                                }
-                            }
+                            const float4 v = *reinterpret_cast<const float4*>(row + c0 + c4);
                             x[c4] = v.x;
                             x[c4 + 1] = v.y;
                             x[c4 + 2] = v.z;
@@ -737,7 +711,6 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     const int rows_tile = kQuarters * (kSlabRows - 2 * p.r);
     MxArgs3D a;
     memset(&a, 0, sizeof(a));
-    a.in = (const float*)src;
     a.bc = p.bc;
     a.bops = p.d_operands;
     a.err = st->err_dev;

@@ -41,6 +41,54 @@ def test_mx_2d_shapes(shape, bc):
     check(got, oracle.gather(a, r, cg, bc, 4), 1e-5, f"mx shape {shape} {bc}")
 
 
+@pytest.mark.parametrize("shape,r,kind", [((3, 64), 1, "box"), ((5, 40), 2, "box"), ((9, 300), 4, "star"),
+                                          ((130, 5), 2, "box"), ((7, 7), 3, "box"), ((300, 9), 4, "box")])
+def test_mx_2d_periodic_at_the_minimum_extent(shape, r, kind):
+    """Extents of 2r + 1 (the smallest a plan takes): the periodic halo of
+    every point wraps across both faces, which the boundary-term kernel adds
+    (the tensor-core kernel reads zeros outside the grid)."""
+    a, cg = problem(2, shape, r, kind, seed=sum(shape) + r)
+    got, info = run(a, r, kind, cg, "f32", "periodic", 3, impl="matrixized", prec="tf32x3")
+    assert info["impl"] == 2 and info["kernels_per_sweep"] == 2 and info["device_error"] == 0
+    check(got, oracle.gather(a, r, cg, "periodic", 3), 1e-5, f"mx small periodic {shape} r={r}")
+
+
+@pytest.mark.parametrize("shape,r,kind,cover", [((3, 3, 64), 1, "box", "auto"), ((3, 40, 3), 1, "star", "hybrid"),
+                                                ((7, 7, 70), 3, "star", "parallel")])
+def test_mx_3d_periodic_at_the_minimum_extent(shape, r, kind, cover):
+    a, cg = problem(3, shape, r, kind, seed=sum(shape) + 7 * r)
+    got, info = run(a, r, kind, cg, "f32", "periodic", 3, impl="matrixized", prec="tf32x3", cover=cover)
+    assert info["impl"] == 2 and info["kernels_per_sweep"] == 2 and info["device_error"] == 0
+    check(got, oracle.gather(a, r, cg, "periodic", 3), 1e-5, f"mx 3d small periodic {shape} r={r}")
+
+
+@pytest.mark.parametrize("ndim,kind", [(2, "box"), (3, "star")])
+def test_kernels_per_sweep(ndim, kind):
+    """One kernel per sweep, plus the boundary-term kernel for periodic
+    matrixized plans; a stencil with no off-centre weight in x or y (pure z
+    line, 3D) needs no boundary terms."""
+    import paper_2310_16298_gb300 as sx
+    shape = (64, 64) if ndim == 2 else (16, 32, 64)
+    cg = si.coeffs_random(ndim, 1, kind, 5, dtype="f32")
+    for impl, bc, want in [("matrixized", "periodic", 2), ("matrixized", "dirichlet", 1), ("gather", "periodic", 1)]:
+        plan = sx.Plan(shape, 1, kind, cg, "f32", bc=bc, impl=impl)
+        try:
+            assert plan.info["kernels_per_sweep"] == want, (impl, bc)
+        finally:
+            plan.close()
+    if ndim == 3:
+        zline = np.zeros((3, 3, 3))
+        zline[:, 1, 1] = [0.25, 0.5, 0.25]
+        plan = sx.Plan(shape, 1, "star", zline, "f32", bc="periodic", impl="matrixized")
+        try:
+            assert plan.info["kernels_per_sweep"] == 1
+        finally:
+            plan.close()
+        a = si.round_to(si.field_uniform(shape, 9), "f32")
+        got, _ = run(a, 1, "star", zline, "f32", "periodic", 2, impl="matrixized", prec="tf32x3")
+        check(got, oracle.gather(a, 1, zline, "periodic", 2), 1e-5, "z line")
+
+
 def test_mx_exact_when_operands_are_tf32():
     """Inputs and weights exactly representable in TF32 (small dyadic values):
     the lo parts vanish and TF32x3 matches the FP32 CUDA-core result to 1e-6."""
