@@ -303,15 +303,20 @@ __device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity) {
     return ptx::mbar_wait(bar, parity, kGatherWait);
 }
 
-// 2D tile: TY x TX outputs per tile, threads (32, kBYT), one strip of kRS
-// rows per thread row.  Narrow tiles keep two stages within about 44 KB, so
-// five CTAs share an SM.
+// 2D tile: TY x TX outputs per tile, threads (32, kBYT), NST stages in the
+// TMA ring (NST - 1 tiles in flight ahead of the one being computed).
+// FP32: 32 x 128, the last sub-step register-blocked (each thread kVR rows x
+// 4 columns: 256 threads cover the tile once), four stages (about 96 KB, two
+// CTAs per SM: six tiles in flight per SM); FP64: 64 x 32, one strip of kRS
+// rows per thread row, two stages.
 template <typename T>
 struct Tile2 {
-    static constexpr int TY = 64;
-    static constexpr int TX = sizeof(T) == 4 ? 64 : 32;
+    static constexpr int TY = sizeof(T) == 4 ? 32 : 64;
+    static constexpr int TX = sizeof(T) == 4 ? 128 : 32;
+    static constexpr int NST = sizeof(T) == 4 ? 4 : 2;
     static constexpr int AL = 16 / (int)sizeof(T);   // TMA x granule (16 bytes)
 };
+constexpr int kVR = 4;   // FP32 last sub-step: rows per thread
 constexpr int kBYT = 8;
 
 struct G2Args {
@@ -323,7 +328,7 @@ struct G2Args {
     int tiles_x, tiles_total;
 };
 
-// Shared-memory layout of the 2D kernel for depth tb: two stages (TMA ring)
+// Shared-memory layout of the 2D kernel for depth tb: NST stages (TMA ring)
 // and, for tb > 1, a work buffer for the sub-step ping-pong; kRS slack rows
 // after each buffer are read (never used) by ragged strips.
 template <typename T>
@@ -336,7 +341,7 @@ struct Layout2 {
         SX = Tile2<T>::TX + 2 * HX;
         buf = round_up((SY + kRS) * SX, 128 / (int)sizeof(T));
     }
-    __host__ __device__ int buffers(int tb) const { return tb > 1 ? 3 : 2; }
+    __host__ __device__ int buffers(int tb) const { return Tile2<T>::NST + (tb > 1 ? 1 : 0); }
     __host__ __device__ size_t bytes(int tb) const { return (size_t)buffers(tb) * buf * sizeof(T) + 64 + 128; }
 };
 
@@ -394,83 +399,229 @@ __device__ __forceinline__ void substep2(const T* src, T* dst, T* __restrict__ o
     }
 }
 
+// Last sub-step of the 2D FP32 tile, register-blocked: a thread computes kRS
+// rows x 4 adjacent columns.  Each input row it needs is read as three 16-byte
+// shared-memory loads (columns x-4 .. x+7, enough for r <= 4), and every
+// weight is applied to four columns at once, so a update costs its P FMAs and
+// about one shared-memory load instruction (the scalar form spends about
+// 7.5 loads and the index arithmetic around them).  Rows of 4 outputs go out
+// as 16-byte stores.  The last sub-step's valid region starts at the aligned
+// column HX and is TX wide, so the column groups are aligned.
+template <int R, bool STAR>
+__device__ __forceinline__ void last_substep2_f32(const float* src, float* __restrict__ out, const Layout2<float>& L,
+                                                  int64_t ny, int64_t nx, int64_t ldx, int64_t y0, int64_t x0,
+                                                  const Coeffs<float, ipow(2 * R + 1, 2)>& cf) {
+    static_assert(R <= 4, "three 16-byte loads cover x-4 .. x+7");
+    constexpr int W = 2 * R + 1;
+    constexpr int kRS = kVR;   // rows per thread here
+    static_assert(Tile2<float>::TY % kRS == 0, "whole strips");
+    const int ncg = Tile2<float>::TX / 4;
+    const int nstrips = Tile2<float>::TY / kRS;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    for (int item = tid; item < nstrips * ncg; item += kBX * kBYT) {
+        const int strip = item / ncg, cgi = item - strip * ncg;   // a warp: consecutive column groups
+        const int sy0 = L.H + strip * kRS;
+        const int sx = L.HX + 4 * cgi;
+        float acc[kRS][4];
+#pragma unroll
+        for (int j = 0; j < kRS; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
+        const float* base = src + (sy0 - R) * L.SX + (sx - 4);
+#pragma unroll
+        for (int yi = 0; yi < kRS + 2 * R; ++yi) {
+            float v[12];   // v[k] = column sx - 4 + k of input row sy0 - R + yi
+#pragma unroll
+            for (int k4 = 0; k4 < 3; ++k4) {
+                const float4 u = *reinterpret_cast<const float4*>(base + yi * L.SX + 4 * k4);
+                v[4 * k4] = u.x;
+                v[4 * k4 + 1] = u.y;
+                v[4 * k4 + 2] = u.z;
+                v[4 * k4 + 3] = u.w;
+            }
+#pragma unroll
+            for (int j = 0; j < kRS; ++j) {
+                const int a = yi - j;
+                if (a >= 0 && a < W) {
+#pragma unroll
+                    for (int b = 0; b < W; ++b)
+                        if (!STAR || a == R || b == R) {
+                            const float w = cf.c[a * W + b];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[j][q] = fmaf(w, v[4 + q + b - R], acc[j][q]);
+                        }
+                }
+            }
+        }
+        const int64_t gx = x0 + 4 * cgi;
+#pragma unroll
+        for (int j = 0; j < kRS; ++j) {
+            const int64_t gy = y0 + strip * kRS + j;
+            if (gy < ny) {
+                float* o = out + gy * ldx + gx;
+                if (gx + 3 < nx) {
+                    *reinterpret_cast<float4*>(o) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (gx + q < nx) o[q] = acc[j][q];
+                }
+            }
+        }
+    }
+}
+
+// i mod n; one add or subtract for the usual halo offsets (|i| < 2n).
+__device__ __forceinline__ int wrap_fast(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
+    const int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// Periodic boundary, 2D tile whose staged block (rows y0 - H .., columns
+// x0 - HX ..) crosses the grid's edge: TMA filled the cells outside the grid
+// with zeros; the CTA overwrites exactly those cells with their wrapped
+// values: the rows outside the grid in full, then the columns outside it in
+// the other rows.  Four loads per thread are in flight at a time.
+template <typename T>
+__device__ __noinline__ void wrap_halo2(T* buf, const Layout2<T>& L, const T* __restrict__ in, int64_t ldx, int ny, int nx, int y0,
+                           int x0) {
+    const int gy0 = y0 - L.H, gx0 = x0 - L.HX;
+    const int top = min(L.SY, max(0, -gy0));          // rows [0, top) lie above the grid
+    const int bot = max(top, min(L.SY, ny - gy0));     // rows [bot, SY) lie below it
+    const int cl = min(L.SX, max(0, -gx0));           // columns [0, cl) left of it
+    const int cr = max(cl, min(L.SX, nx - gx0));      // columns [cr, SX) right of it
+    const int ncx = cl + (L.SX - cr);                 // outside columns per inside row
+    const int n_rows = (top + (L.SY - bot)) * L.SX;   // cells of the outside rows
+    const int n_all = n_rows + (bot - top) * ncx;
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int i0 = tid; i0 < n_all; i0 += 4 * nthr) {
+        T v[4];
+        int off[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nthr;
+            off[u] = -1;
+            v[u] = T(0);
+            if (i < n_all) {
+                int sy, sx;
+                if (i < n_rows) {
+                    const int rr = i / L.SX;
+                    sy = rr < top ? rr : bot + (rr - top);
+                    sx = i - rr * L.SX;
+                } else {
+                    const int j = i - n_rows, rr = j / ncx, c = j - rr * ncx;
+                    sy = top + rr;
+                    sx = c < cl ? c : cr + (c - cl);
+                }
+                off[u] = sy * L.SX + sx;
+                v[u] = in[(int64_t)wrap_fast(gy0 + sy, ny) * ldx + wrap_fast(gx0 + sx, nx)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (off[u] >= 0) buf[off[u]] = v[u];
+    }
+}
+
 // Register budgets of the persistent kernels: left alone, the compiler keeps
 // the coefficients and unrolled sums in registers and one CTA fills an SM.
+// (2D: two CTAs of four-stage rings fill the shared memory; r = 4 stars get
+// the registers of one CTA, which at two spill some 600 bytes.)
 template <typename T, int NDIM>
-constexpr int min_ctas() { return sizeof(T) == 4 ? (NDIM == 2 ? 3 : 4) : 2; }
+constexpr int min_ctas() { return sizeof(T) == 4 ? (NDIM == 2 ? 2 : 4) : 2; }
 
 template <typename T, int R, bool STAR>
-__global__ void __launch_bounds__(kBX * kBYT, min_ctas<T, 2>())
+__global__ void __launch_bounds__(kBX * kBYT, (STAR && R >= 4) ? 1 : min_ctas<T, 2>())
 gather2d_tma_kernel(const __grid_constant__ CUtensorMap tin, const G2Args a, const Coeffs<T, ipow(2 * R + 1, 2)> cf) {
     constexpr int TY = Tile2<T>::TY, TX = Tile2<T>::TX;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = (unsigned char*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
     const Layout2<T> L(R, a.tb);
-    T* stage[2] = {reinterpret_cast<T*>(smem_raw), reinterpret_cast<T*>(smem_raw) + L.buf};
-    T* work = reinterpret_cast<T*>(smem_raw) + 2 * L.buf;
+    constexpr int NST = Tile2<T>::NST;
+    T* const stage0 = reinterpret_cast<T*>(smem_raw);
+    T* work = stage0 + NST * L.buf;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)L.buffers(a.tb) * L.buf * sizeof(T));
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(full + NST);
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const T* in = (const T*)a.in;
     T* out = (T*)a.out;
     const uint32_t box_bytes = (uint32_t)(L.SY * L.SX * sizeof(T));
     if (tid == 0) {
-        ptx::mbar_init(&full[0], 1);
-        ptx::mbar_init(&full[1], 1);
+        for (int i = 0; i < NST; ++i) ptx::mbar_init(&full[i], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
     __syncthreads();
-    // A tile is staged by TMA unless the boundary is periodic and its halo
-    // block crosses the grid's edge.
-    auto by_tma = [&](int t) {
-        if (a.bc != kBcPeriodic) return true;
+    // Every tile is staged by TMA; with a periodic boundary, a tile whose
+    // staged block crosses the grid's edge then gets its outside cells wrapped.
+    auto edge = [&](int t) {
+        if (a.bc != kBcPeriodic) return false;
         const int y0 = (t / a.tiles_x) * TY, x0 = (t % a.tiles_x) * TX;
-        return y0 - L.H >= 0 && y0 + TY + L.H <= a.ny && x0 - L.HX >= 0 && x0 + TX + L.HX <= a.nx;
+        return !(y0 - L.H >= 0 && y0 + TY + L.H <= a.ny && x0 - L.HX >= 0 && x0 + TX + L.HX <= a.nx);
     };
+    // Thread 0 tracks the ring: bit s of `inflight` = a load into stage s not
+    // yet waited for, bit s of `phase` = parity of stage s's next completion.
+    uint32_t inflight = 0, phase = 0;
     auto issue = [&](int t, int s) {
+        if (t >= a.tiles_total) return;
         const int y0 = (t / a.tiles_x) * TY, x0 = (t % a.tiles_x) * TX;
         ptx::mbar_arrive_expect_tx(&full[s], box_bytes);
-        ptx::tma_load_2d(stage[s], &tin, x0 - L.HX, y0 - L.H, &full[s]);
+        ptx::tma_load_2d(stage0 + s * L.buf, &tin, x0 - L.HX, y0 - L.H, &full[s]);
+        inflight |= 1u << s;
     };
-    int uses[2] = {0, 0};   // TMA loads into each stage so far (mbarrier phases)
-    int pending = -1;       // stage with a TMA load in flight that nobody waited for yet
     const int first = blockIdx.x;
-    if (tid == 0 && first < a.tiles_total && by_tma(first)) issue(first, 0);
+    if (tid == 0)
+        for (int i = 0; i < NST - 1; ++i) issue(first + i * (int)gridDim.x, i);
     int k = 0;
     for (int t = first; t < a.tiles_total; t += gridDim.x, ++k) {
-        const int s = k & 1;
-        const int tn = t + gridDim.x;
-        if (tn < a.tiles_total && by_tma(tn)) {
-            if (tid == 0) issue(tn, s ^ 1);
-            pending = s ^ 1;
-        } else {
-            pending = -1;
+        const int s = k % NST;
+        T* st_buf = stage0 + s * L.buf;
+        // the stage computed at iteration k - 1 is free (barrier at its end);
+        // its generic-proxy writes (element path, sub-steps) are ordered
+        // before the TMA write that refills it
+        if (tid == 0) {
+            ptx::fence_proxy_async_smem();
+            issue(t + (NST - 1) * (int)gridDim.x, (k + NST - 1) % NST);
         }
         const int64_t y0 = (int64_t)(t / a.tiles_x) * TY, x0 = (int64_t)(t % a.tiles_x) * TX;
-        if (by_tma(t)) {
-            if (!gwait(&full[s], (uint32_t)(uses[s] & 1))) *abort_flag = 1;
-            ++uses[s];
-        } else {
-            // element path: wrapped indices (periodic boundary)
-            for (int sy = threadIdx.y; sy < L.SY; sy += kBYT)
-                for (int sx = threadIdx.x; sx < L.SX; sx += kBX)
-                    stage[s][sy * L.SX + sx] =
-                        in[wrap_index(y0 - L.H + sy, a.ny) * a.ldx + wrap_index(x0 - L.HX + sx, a.nx)];
+        {
+            const uint32_t par = (phase >> s) & 1u;   // every thread tracks the parities
+            if (!gwait(&full[s], par)) *abort_flag = 1;
+            phase ^= 1u << s;
+            if (tid == 0) inflight &= ~(1u << s);
+        }
+        if (edge(t)) {
+            __syncthreads();   // every thread has seen the load land (or the abort)
+            if (!*abort_flag) wrap_halo2<T>(st_buf, L, in, a.ldx, a.ny, a.nx, (int)y0, (int)x0);
         }
         __syncthreads();
         if (*abort_flag) break;
-        T* bufs[2] = {stage[s], work};
+        T* src = st_buf;
         for (int st = 1; st <= a.tb; ++st) {
-            substep2<T, R, STAR>(bufs[(st - 1) & 1], bufs[st & 1], out, L, st, st == a.tb, a.ny, a.nx, a.ldx, a.bc, y0,
-                                 x0, cf);
-            __syncthreads();   // sub-step st is complete (and, after the last, stage s is free)
+            T* dst = (st & 1) ? work : st_buf;   // sub-steps alternate between the work buffer and the stage
+            if constexpr (sizeof(T) == 4) {
+                if (st == a.tb)
+                    last_substep2_f32<R, STAR>(src, out, L, a.ny, a.nx, a.ldx, y0, x0, cf);
+                else
+                    substep2<T, R, STAR>(src, dst, out, L, st, false, a.ny, a.nx, a.ldx, a.bc, y0, x0, cf);
+            } else {
+                substep2<T, R, STAR>(src, dst, out, L, st, st == a.tb, a.ny, a.nx, a.ldx, a.bc, y0, x0, cf);
+            }
+            src = dst;
+            __syncthreads();   // sub-step st is complete (and, after the last, the stage is free)
         }
     }
     if (*abort_flag) {
-        // let a load still in flight land before the CTA gives up its shared memory
-        if (tid == 0 && pending >= 0) ptx::mbar_wait(&full[pending], (uint32_t)(uses[pending] & 1), kGatherWait / 8);
-        if (tid == 0 && a.err) atomicOr(a.err, 2u);
+        // let the loads still in flight land before the CTA gives up its shared memory
+        if (tid == 0) {
+            for (int s2 = 0; s2 < NST; ++s2)
+                if ((inflight >> s2) & 1u) ptx::mbar_wait(&full[s2], (phase >> s2) & 1u, kGatherWait / 8);
+            if (a.err) atomicOr(a.err, 2u);
+        }
     }
 }
 
