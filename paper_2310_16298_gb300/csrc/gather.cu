@@ -480,21 +480,23 @@ __device__ __forceinline__ int wrap_fast(int i, int n) {
     return m < 0 ? m + n : m;
 }
 
-// Periodic boundary, 2D tile whose staged block (rows y0 - H .., columns
-// x0 - HX ..) crosses the grid's edge: TMA filled the cells outside the grid
-// with zeros; the CTA overwrites exactly those cells with their wrapped
-// values: the rows outside the grid in full, then the columns outside it in
-// the other rows.  Four loads per thread are in flight at a time.
+// Periodic boundary, a staged block (SY rows x SX columns, cell (0, 0) =
+// grid point (gy0, gx0) of the plane `in`) that crosses the grid's edge: TMA
+// filled the cells outside the grid with zeros; the CTA overwrites exactly
+// those cells with their wrapped values: the rows outside the grid in full,
+// then the columns outside it in the other rows.  Four loads per thread are
+// in flight at a time.  The 2D kernel calls it out of line (inlined, it
+// raised the register pressure of the whole kernel); in the 3D kernel, whose
+// budget is 64 registers, a call cost more spills than the inlined copy.
 template <typename T>
-__device__ __noinline__ void wrap_halo2(T* buf, const Layout2<T>& L, const T* __restrict__ in, int64_t ldx, int ny, int nx, int y0,
-                           int x0) {
-    const int gy0 = y0 - L.H, gx0 = x0 - L.HX;
-    const int top = min(L.SY, max(0, -gy0));          // rows [0, top) lie above the grid
-    const int bot = max(top, min(L.SY, ny - gy0));     // rows [bot, SY) lie below it
-    const int cl = min(L.SX, max(0, -gx0));           // columns [0, cl) left of it
-    const int cr = max(cl, min(L.SX, nx - gx0));      // columns [cr, SX) right of it
-    const int ncx = cl + (L.SX - cr);                 // outside columns per inside row
-    const int n_rows = (top + (L.SY - bot)) * L.SX;   // cells of the outside rows
+__device__ __forceinline__ void wrap_halo_block_inl(T* buf, int SY, int SX, const T* __restrict__ in, int64_t ldx,
+                                                    int ny, int nx, int gy0, int gx0) {
+    const int top = min(SY, max(0, -gy0));          // rows [0, top) lie above the grid
+    const int bot = max(top, min(SY, ny - gy0));     // rows [bot, SY) lie below it
+    const int cl = min(SX, max(0, -gx0));           // columns [0, cl) left of it
+    const int cr = max(cl, min(SX, nx - gx0));      // columns [cr, SX) right of it
+    const int ncx = cl + (SX - cr);                 // outside columns per inside row
+    const int n_rows = (top + (SY - bot)) * SX;     // cells of the outside rows
     const int n_all = n_rows + (bot - top) * ncx;
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -509,15 +511,15 @@ __device__ __noinline__ void wrap_halo2(T* buf, const Layout2<T>& L, const T* __
             if (i < n_all) {
                 int sy, sx;
                 if (i < n_rows) {
-                    const int rr = i / L.SX;
+                    const int rr = i / SX;
                     sy = rr < top ? rr : bot + (rr - top);
-                    sx = i - rr * L.SX;
+                    sx = i - rr * SX;
                 } else {
                     const int j = i - n_rows, rr = j / ncx, c = j - rr * ncx;
                     sy = top + rr;
                     sx = c < cl ? c : cr + (c - cl);
                 }
-                off[u] = sy * L.SX + sx;
+                off[u] = sy * SX + sx;
                 v[u] = in[(int64_t)wrap_fast(gy0 + sy, ny) * ldx + wrap_fast(gx0 + sx, nx)];
             }
         }
@@ -525,6 +527,12 @@ __device__ __noinline__ void wrap_halo2(T* buf, const Layout2<T>& L, const T* __
         for (int u = 0; u < 4; ++u)
             if (off[u] >= 0) buf[off[u]] = v[u];
     }
+}
+
+template <typename T>
+__device__ __noinline__ void wrap_halo_block(T* buf, int SY, int SX, const T* __restrict__ in, int64_t ldx, int ny,
+                                             int nx, int gy0, int gx0) {
+    wrap_halo_block_inl<T>(buf, SY, SX, in, ldx, ny, nx, gy0, gx0);
 }
 
 // Register budgets of the persistent kernels: left alone, the compiler keeps
@@ -596,7 +604,8 @@ gather2d_tma_kernel(const __grid_constant__ CUtensorMap tin, const G2Args a, con
         }
         if (edge(t)) {
             __syncthreads();   // every thread has seen the load land (or the abort)
-            if (!*abort_flag) wrap_halo2<T>(st_buf, L, in, a.ldx, a.ny, a.nx, (int)y0, (int)x0);
+            if (!*abort_flag)
+                wrap_halo_block<T>(st_buf, L.SY, L.SX, in, a.ldx, a.ny, a.nx, (int)y0 - L.H, (int)x0 - L.HX);
         }
         __syncthreads();
         if (*abort_flag) break;
@@ -686,44 +695,44 @@ gather3d_stream_kernel(const __grid_constant__ CUtensorMap tin, const G3Args a, 
         const int tx_ = u % a.tiles_x, ty_ = (u / a.tiles_x) % a.tiles_y, tz_ = u / (a.tiles_x * a.tiles_y);
         const int x0 = tx_ * TX, y0 = ty_ * TY, z0 = tz_ * TZC;
         const int nout = min(TZC, a.nz - z0);
-        const bool tma = a.bc != kBcPeriodic ||
-                         (y0 - R >= 0 && y0 + TY + R <= a.ny && x0 - L::HX >= 0 && x0 + TX + L::HX <= a.nx);
+        // with a periodic boundary, an edge unit's planes (staged by TMA like
+        // the others, from the wrapped plane index) get their cells outside
+        // the grid in y and x wrapped once they have landed
+        const bool edge = a.bc == kBcPeriodic &&
+                          !(y0 - R >= 0 && y0 + TY + R <= a.ny && x0 - L::HX >= 0 && x0 + TX + L::HX <= a.nx);
         // input plane i of the unit is grid plane z0 - R + i, held in buffer i % NPL
         auto load = [&](int i) {
             const int b = i % NPL;
             int gz = z0 - R + i;
             if (a.bc == kBcPeriodic) gz = (int)wrap_index(gz, a.nz);
-            if (tma) {
-                if (tid == 0) {
-                    ptx::mbar_arrive_expect_tx(&full[b], box_bytes);
-                    ptx::tma_load_3d(planes + b * L::PLANE, &tin, x0 - L::HX, y0 - R, gz, &full[b]);
-                }
-                in_flight |= 1u << b;
-            } else {
-                T* dst = planes + b * L::PLANE;
-                for (int e = tid; e < L::SY * L::SX; e += kThreads3) {
-                    const int sy = e / L::SX, sx = e % L::SX;
-                    dst[e] = in[((int64_t)gz * a.ny + wrap_index(y0 - R + sy, a.ny)) * a.ldx +
-                                wrap_index(x0 - L::HX + sx, a.nx)];
-                }
+            if (tid == 0) {
+                ptx::fence_proxy_async_smem();   // after the fix-ups of the plane it replaces
+                ptx::mbar_arrive_expect_tx(&full[b], box_bytes);
+                ptx::tma_load_3d(planes + b * L::PLANE, &tin, x0 - L::HX, y0 - R, gz, &full[b]);
             }
+            in_flight |= 1u << b;
         };
         auto ready = [&](int i) {   // input plane i is in its buffer
             const int b = i % NPL;
-            if (tma) {
-                if (!gwait(&full[b], (uint32_t)(uses[b] & 1))) *abort_flag = 1;
-                ++uses[b];
-                in_flight &= ~(1u << b);
-            }
+            if (!gwait(&full[b], (uint32_t)(uses[b] & 1))) *abort_flag = 1;
+            ++uses[b];
+            in_flight &= ~(1u << b);
+        };
+        auto wrap_plane = [&](int i) {
+            int gz = z0 - R + i;
+            gz = (int)wrap_index(gz, a.nz);
+            wrap_halo_block_inl<T>(planes + (i % NPL) * L::PLANE, L::SY, L::SX, in + (int64_t)gz * a.ny * a.ldx,
+                                   a.ldx, a.ny, a.nx, y0 - R, x0 - L::HX);
         };
         const int nin = nout + 2 * R;
         for (int i = 0; i < NPL && i < nin; ++i) load(i);
-        if (!tma) __syncthreads();
         for (int o = 0; o < nout; ++o) {
-            if (o == 0) {
-                for (int i = 0; i < 2 * R + 1; ++i) ready(i);
-            } else {
-                ready(o + 2 * R);
+            const int i_lo = o == 0 ? 0 : o + 2 * R;   // planes that land now
+            for (int i = i_lo; i <= o + 2 * R; ++i) ready(i);
+            if (edge) {
+                __syncthreads();   // every thread has seen the planes land (or the abort)
+                if (*abort_flag) break;
+                for (int i = i_lo; i <= o + 2 * R; ++i) wrap_plane(i);
             }
             __syncthreads();
             if (*abort_flag) break;
@@ -768,10 +777,7 @@ gather3d_stream_kernel(const __grid_constant__ CUtensorMap tin, const G3Args a, 
                 }
             }
             __syncthreads();   // input plane o is no longer needed: its buffer takes plane o + NPL
-            if (o + NPL < nin) {
-                load(o + NPL);
-                if (!tma) __syncthreads();
-            }
+            if (o + NPL < nin) load(o + NPL);
         }
         // planes loaded but not needed (short last chunk) are waited for before reuse
         for (int b = 0; b < NPL; ++b)
