@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box25-8192",
-                    choices=["box25-8192", "star7-512", "box27-512", "sine7-512", "sine27-512", "jacobi-256",
+                    choices=["box25-8192", "star7-512", "box27-512", "box125-512", "sine7-512", "sine27-512", "jacobi-256",
                              "batch-1024", "serve-2000", "error-growth", "cover-study", "ablation"])
     ap.add_argument("--batch", type=int, default=1024, help="problems in the batch workload")
     ap.add_argument("--side", type=int, default=0, help="grid side (0 = the workload's own)")
@@ -76,6 +76,8 @@ def base_workload(args):
         return si.cube_512(si.STAR, args.dtype or "f32", args.tsteps or 50, args.side or 512)
     if w == "box27-512":
         return si.cube_512(si.BOX, args.dtype or "f32", args.tsteps or 50, args.side or 512)
+    if w == "box125-512":
+        return si.cube_512(si.BOX, args.dtype or "f32", args.tsteps or 50, args.side or 512, r=2)
     if w == "sine7-512":
         return si.sine_cube_512(si.STAR, args.tsteps or 1000, args.side or 512)
     if w == "sine27-512":
@@ -91,6 +93,7 @@ def workload(args):
 
 def workload_config(p, args, extra=None):
     desc = {"box25-8192": "2D box r=2 (25-point)", "star7-512": "3D 7-point star", "box27-512": "3D 27-point box",
+            "box125-512": "3D box r=2 (125-point)",
             "sine7-512": "3D 7-point star (centre 0.4, neighbours 0.1)",
             "sine27-512": "3D 27-point separable box ((1/4,1/2,1/4)^3)",
             "jacobi-256": "2D 5-point Jacobi star"}[args.workload]

@@ -32,7 +32,7 @@ namespace stx {
 
 namespace {
 
-constexpr int kMaxEdgeTerms = 80;   // (2r + 1)^2 - 1 for r = 4; the 3D kernels stop below it
+constexpr int kMaxEdgeTerms = 120;   // 2D r = 4: (2r+1)^2 - 1 = 80; 3D r = 2 box: (2r+1)^3 - (2r+1) = 120
 
 struct EdgeTerm {
     int8_t dz, dy, dx, pad;

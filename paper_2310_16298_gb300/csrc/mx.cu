@@ -636,7 +636,7 @@ static stencil_status with_edges(const MxRequest& q, MxPlan* p, std::string* why
     const stencil_status s = mx_edges_build(q, p);
     if (s != STENCIL_OK) {
         mx_plan_free(p);
-        if (why) *why = "the periodic boundary-term table holds r <= 4 and at most 80 terms";
+        if (why) *why = "the periodic boundary-term table holds r <= 4 and at most 120 terms";
     }
     return s;
 }

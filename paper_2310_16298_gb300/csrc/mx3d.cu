@@ -75,15 +75,20 @@ template <bool BF>
 __host__ __device__ constexpr int a_stage_cols3(int nb) {
     return OpFmt<BF>::kMaxParts * OpFmt<BF>::part_cols(OpFmt<BF>::window(nb));
 }
+// Output columns per tile: 32 where the lines' accumulators fit twice beside
+// two A stages, else 16, else 8 (the 125-point box: 25 lines).
 template <bool BF>
 __host__ __device__ constexpr int tile_nb3(int L) {
-    return (L * 32 <= 256 && 2 * L * 32 + 2 * a_stage_cols3<BF>(32) <= kTmemCols) ? 32 : 16;
+    return (L * 32 <= 256 && 2 * L * 32 + 2 * a_stage_cols3<BF>(32) <= kTmemCols) ? 32 : (L * 16 <= 256 ? 16 : 8);
 }
+// Lines as the MMA sees them: N = lines x nb must be a multiple of 16 (M =
+// 128), so an odd line count at 8 columns gets one all-zero line.
+__host__ __device__ constexpr int mma_lines3(int L, int nb) { return ((L * nb + 15) / 16) * 16 / nb; }
 // Raw plane slabs: K window widened to an odd number of 16-byte chunks
 // (conflict-free 16-byte row loads, as in the 2D kernel).
 __host__ __device__ constexpr int raw_pitch3(int k) { return ((k / 4) & 1) ? k : k + 4; }
 __host__ __device__ constexpr int raw_stage_bytes3(int pitch) { return kQuarters * kSlabRows * pitch * 4; }
-// Output staging: two buffers of (32 - 2r) rows x NB/2 floats per epilogue warp.
+// Output staging: two buffers of 32 rows x NB/2 floats per epilogue warp.
 __host__ __device__ constexpr int out_warp_bytes3(int nb) { return ((32 * (nb / kSubs) * 4) + 1023) / 1024 * 1024; }
 __host__ __device__ constexpr int out_bytes3(int nb) { return kRoleWarps * 2 * out_warp_bytes3(nb); }
 __host__ __device__ constexpr int window3(int nb, bool bf) {
@@ -129,7 +134,8 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     static_assert(!HYB || (STAR && 4 * R <= 12), "hybrid cover: star stencils, r <= 3");
     using F = OpFmt<BF>;
     constexpr int L = LN::L;
-    constexpr int N = L * NB;
+    constexpr int LM = mma_lines3(L, NB);   // lines on the MMA (L, or L + 1 zero line)
+    constexpr int N = LM * NB;
     constexpr int K = F::window(NB);
     constexpr int KS = K / F::kKStep;
     constexpr int GW = F::kGroup;
@@ -140,7 +146,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
     constexpr int CW = NB / kSubs;
     constexpr int KP = raw_pitch3(K);
     constexpr int RSB = raw_stage_bytes3(KP);
-    constexpr int kRawStages = raw_stages3(NB, L, BF);
+    constexpr int kRawStages = raw_stages3(NB, LM, BF);
     constexpr int OWB = out_warp_bytes3(NB);
     const int PLANES = args.chunk + 2 * R;  // input planes per work unit
     constexpr uint32_t SLAB_BOX = (uint32_t)(kSlabRows * KP * 4);
@@ -400,6 +406,7 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                         // line (a, b): rows shift by b - R, target output plane slot 2R - a.
                         // Lines are drained in batches of LB to bound live registers.
                         constexpr int LB = (CW == 16) ? 2 : 4;
+                        static_assert(CW == 16 || CW == 8 || CW == 4, "epilogue column share");
     #pragma unroll
                         for (int l0 = 0; l0 < L; l0 += LB) {
                             uint32_t v[LB][CW];
@@ -408,6 +415,12 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
                             if constexpr (CW == 16) {
                                 if (nv == 2) ptx::tmem_ld_x16_sync(ba, v[0], ba + NB, v[1]);
                                 if (nv == 1) ptx::tmem_ld_x16_sync(ba, v[0]);
+                            } else if constexpr (CW == 4) {
+                                if (nv == 4)
+                                    ptx::tmem_ld_x4_sync(ba, v[0], ba + NB, v[1], ba + 2 * NB, v[2], ba + 3 * NB, v[3]);
+                                if (nv == 3) ptx::tmem_ld_x4_sync(ba, v[0], ba + NB, v[1], ba + 2 * NB, v[2]);
+                                if (nv == 2) ptx::tmem_ld_x4_sync(ba, v[0], ba + NB, v[1]);
+                                if (nv == 1) ptx::tmem_ld_x4_sync(ba, v[0]);
                             } else {
                                 if constexpr (LB >= 4) {
                                     if (nv == 4)
@@ -447,7 +460,11 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
 #pragma unroll
                             for (int c = 0; c < CW; c += 4) {
                                 const int chunk = c >> 2;
-                                const int sw = (CW == 16) ? (chunk ^ ((orow >> 1) & 3)) : (chunk ^ ((orow >> 2) & 1));
+                                // the output map's swizzle: 64B for 64-byte rows, 32B for
+                                // 32-byte rows, none for 16-byte rows
+                                const int sw = (CW == 16)  ? (chunk ^ ((orow >> 1) & 3))
+                                               : (CW == 8) ? (chunk ^ ((orow >> 2) & 1))
+                                                           : chunk;
                                 *reinterpret_cast<float4*>(ost + orow * (CW * 4) + sw * 16) =
                                     make_float4(acc[0][c], acc[0][c + 1], acc[0][c + 2], acc[0][c + 3]);
                             }
@@ -530,8 +547,9 @@ Mx3Kernel kernel3_for(int r, bool star, bool bf, bool hyb) {
             case 2: return kernel3_star<2>(bf, hyb);
             case 3: return kernel3_star<3>(bf, hyb);
         }
-    } else if (r == 1 && !hyb) {
-        return bf ? kernel3<1, false, true, false>() : kernel3<1, false, false, false>();
+    } else if (!hyb) {
+        if (r == 1) return bf ? kernel3<1, false, true, false>() : kernel3<1, false, false, false>();
+        if (r == 2) return bf ? kernel3<2, false, true, false>() : kernel3<2, false, false, false>();
     }
     return nullptr;
 }
@@ -571,7 +589,8 @@ bool encode_out_map_3d(CUtensorMap* map, float* base, int nz, int ny, int nx, in
     cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE,
+               cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : cols == 8 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -605,7 +624,7 @@ bool mx3d_supported(const MxRequest& q, std::string* why) {
         return false;
     }
     if (!kernel3_for(q.r, q.star, false, use_hybrid(q))) {
-        if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27-point box";
+        if (why) *why = "3D matrixized kernel built for 7/13/19-point stars (r <= 3) and the 27- and 125-point boxes";
         return false;
     }
     if (q.ldx % 4 != 0) {
@@ -638,6 +657,9 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
         for (int l = 0; l < L; ++l)
             lines.push_back(q.cg + ((size_t)line3_a(r, q.star, l) * W + line3_b(r, q.star, l)) * W);
     }
+    const int LM = mma_lines3(L, NB);
+    std::vector<double> zero_line(W, 0.0);   // pads N to a multiple of 16
+    while ((int)lines.size() < LM) lines.push_back(zero_line.data());
     uint32_t bpart = 0;
     std::vector<unsigned char> ops = pack_bands(r, lines, NB, KW, bf, &bpart);
     p->n_lines = L;
@@ -671,10 +693,10 @@ stencil_status mx3d_plan_build(const MxRequest& q, MxPlan* p, std::string* why) 
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess && st->bop_bytes != (uint32_t)bop_bytes3(NB, L, bf)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && st->bop_bytes != (uint32_t)bop_bytes3(NB, LM, bf)) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel3_for(r, q.star, bf, hyb), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_bytes_3d(NB, L, bf));
+                                 smem_bytes_3d(NB, LM, bf));
     p->tmap_storage = st;
     if (e != cudaSuccess) {
         if (why) *why = std::string("3D plan set-up: ") + cudaGetErrorString(e);
@@ -734,7 +756,7 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
         return cudaErrorInvalidValue;
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
     for (int k = 0; k < 12; ++k) a.sw[k] = st->sw[k];
-    const int smem = smem_bytes_3d(st->nb, lines3(p.r, st->star, st->hyb), st->bf);
+    const int smem = smem_bytes_3d(st->nb, mma_lines3(lines3(p.r, st->star, st->hyb), st->nb), st->bf);
     kernel3_for(p.r, st->star, st->bf, st->hyb)<<<grid, kThreads, smem, s>>>(map, map_out, a);
     return cudaGetLastError();
 }

@@ -201,6 +201,49 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 //
 // tmem_ld_xW_sync(a0, r0, a1, r1, ...): 32 lanes x W consecutive 32-bit
 // columns from each address; thread t of the warp receives lane (base + t).
+// 4 columns per block (32x32b.x4), 1-4 blocks, then the wait.
+__device__ __forceinline__ void tmem_ld_x4_sync(uint32_t a0, uint32_t (&r0)[4]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3])
+        : "r"(a0)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x4_sync(uint32_t a0, uint32_t (&r0)[4], uint32_t a1, uint32_t (&r1)[4]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%8];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%9];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3])
+        : "r"(a0), "r"(a1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x4_sync(uint32_t a0, uint32_t (&r0)[4], uint32_t a1, uint32_t (&r1)[4], uint32_t a2, uint32_t (&r2)[4]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%13];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%14];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3])
+        : "r"(a0), "r"(a1), "r"(a2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x4_sync(uint32_t a0, uint32_t (&r0)[4], uint32_t a1, uint32_t (&r1)[4], uint32_t a2, uint32_t (&r2)[4], uint32_t a3, uint32_t (&r3)[4]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%17];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%18];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%19];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r3[0]), "=r"(r3[1]), "=r"(r3[2]), "=r"(r3[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_x8_sync(uint32_t a0, uint32_t (&r0)[8]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"

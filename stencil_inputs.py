@@ -199,12 +199,13 @@ def box25_8192(dtype: str = "f32", steps: int = 100, side: int = 8192) -> Proble
                    PERIODIC, steps, 2, name=f"2d25p-box-{side}-{dtype}")
 
 
-def cube_512(kind: str, dtype: str = "f32", steps: int = 50, side: int = 512) -> Problem:
-    """3D 7-point star or 27-point box, side^3, interior uniform[-1,1), zero
-    Dirichlet halo, random normalised coefficients (seed 103)."""
-    return Problem(3, (side,) * 3, 1, kind, coeffs_random(3, 1, kind, 103, dtype=dtype), dtype,
-                   DIRICHLET, steps, 3, -1.0, 1.0,
-                   name=f"3d{'7' if kind == STAR else '27'}p-{side}-{dtype}")
+def cube_512(kind: str, dtype: str = "f32", steps: int = 50, side: int = 512, r: int = 1) -> Problem:
+    """3D star or box of order r (7-point star and 27-point box at r = 1),
+    side^3, interior uniform[-1,1), zero Dirichlet halo, random normalised
+    coefficients (seed 103)."""
+    points = 6 * r + 1 if kind == STAR else (2 * r + 1) ** 3
+    return Problem(3, (side,) * 3, r, kind, coeffs_random(3, r, kind, 103, dtype=dtype), dtype,
+                   DIRICHLET, steps, 3, -1.0, 1.0, name=f"3d{points}p-{side}-{dtype}")
 
 
 def batch_1024(n: int = 1024, seed: int = 4, lo: int = 64, hi: int = 2048,

@@ -95,6 +95,17 @@ def workload_problem(shape, r, kind, lo):
     return a, cg
 
 
+def test_mx_3d_125_point_box_more_units_than_sms():
+    """96 x 240 x 256, r = 2 box: 3 chunks x 3 y tiles (112 rows) x 32 x
+    tiles (8 columns) = 288 work units."""
+    shape, r, steps = (96, 240, 256), 2, 2
+    a, cg = problem(shape, r, "box", 40, lo=-1.0, hi=1.0)
+    got, info = run(a, r, "box", cg, "f32", "dirichlet", steps, impl="matrixized", prec="tf32x3")
+    assert info["impl"] == 2 and info["tile_n"] == 8
+    assert 3 * 3 * (256 // 8) > num_sms()
+    check(got, oracle.gather(a, r, cg, "dirichlet", steps), 1e-5, "125-point box, many units")
+
+
 FULL_RUNS = [((2048, 2048), 2, "box", "periodic", 100, 0.0),
              ((160, 256, 256), 1, "star", "dirichlet", 50, -1.0),
              ((160, 256, 256), 1, "box", "dirichlet", 50, -1.0)]

@@ -89,6 +89,17 @@ def test_kernels_per_sweep(ndim, kind):
         check(got, oracle.gather(a, 1, zline, "periodic", 2), 1e-5, "z line")
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_mx_3d_125_point_box_runs_on_the_tensor_cores(prec):
+    """The 3D box of order 2: 25 lines of 8 columns plus one all-zero line
+    (N = 208, a multiple of 16), five running plane sums."""
+    shape = (37, 61, 52)
+    a, cg = problem(3, shape, 2, "box", seed=125)
+    got, info = run(a, 2, "box", cg, "f32", "dirichlet", 2, impl="matrixized", prec=prec)
+    assert info["impl"] == 2 and info["n_lines"] == 25 and info["tile_n"] == 8
+    check(got, oracle.gather(a, 2, cg, "dirichlet", 2), TOL[prec], f"125-point box {prec}")
+
+
 def test_mx_exact_when_operands_are_tf32():
     """Inputs and weights exactly representable in TF32 (small dyadic values):
     the lo parts vanish and TF32x3 matches the FP32 CUDA-core result to 1e-6."""
@@ -138,7 +149,7 @@ def test_mx_takes_unaligned_rows_through_padded_grids():
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16x3", "bf16", "bf16w2"])
-@pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("star", 3)])
+@pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("star", 3), ("box", 2)])
 @pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
 def test_mx_3d(prec, kind, r, shape):
     """3D matrixized sweep (plane streaming, lines along N) vs the oracle:
@@ -252,7 +263,7 @@ def test_arbitrary_weight_patterns(pattern, impl):
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32"])
 @pytest.mark.parametrize("kind,r,cover", [("star", 1, "hybrid"), ("star", 1, "parallel"), ("box", 1, "auto"),
-                                          ("star", 2, "hybrid"), ("star", 3, "parallel")])
+                                          ("star", 2, "hybrid"), ("star", 3, "parallel"), ("box", 2, "auto")])
 @pytest.mark.parametrize("shape", [(40, 150, 44), (70, 29, 68)])
 def test_mx_3d_periodic(prec, kind, r, cover, shape):
     """Periodic 3D sweeps: wrapped plane indices and wrapped halo rows and
@@ -263,7 +274,7 @@ def test_mx_3d_periodic(prec, kind, r, cover, shape):
     check(got, oracle.gather(a, r, cg, "periodic", 3), TOL[prec], f"mx 3d periodic {kind} r={r} {cover} {prec}")
 
 
-@pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2)])
+@pytest.mark.parametrize("kind,r", [("star", 1), ("box", 1), ("star", 2), ("box", 2)])
 def test_mx_3d_unit_depth_does_not_change_the_result(kind, r):
     """The work-unit depth (planes per unit) changes how often halo planes
     are re-read, not the arithmetic: every output plane sums the same input
