@@ -20,10 +20,11 @@ def run_bench(args, env_extra=None):
     return r.stdout
 
 
-@pytest.mark.parametrize("workload,side", [("box25-8192", 192), ("star7-512", 24)])
-def test_reference_arm_line(workload, side):
+@pytest.mark.parametrize("workload,side,extra", [("box25-8192", 192, []), ("star7-512", 24, []),
+                                                ("box125-512", 16, []), ("star7-512", 20, ["--bc", "periodic"])])
+def test_reference_arm_line(workload, side, extra):
     out = run_bench(["--impl", "reference", "--workload", workload, "--side", str(side), "--steps", "2",
-                     "--warmup", "1"])
+                     "--warmup", "1"] + extra)
     line = json.loads(out.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
@@ -44,3 +45,22 @@ def test_reference_arm_other_ranks_print_nothing():
     out = run_bench(["--impl", "reference", "--side", "64", "--steps", "1", "--warmup", "0"],
                     {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out.strip() == ""
+
+
+def test_workload_options():
+    """--bc overrides the workload's boundary; box125-512 is the order-2 3D box."""
+    sys.path.insert(0, ROOT)
+    import bench
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py", "--workload", "star7-512", "--bc", "periodic", "--side", "12"]
+        p = bench.workload(bench.parse())
+        assert p.bc == "periodic" and p.shape == (12, 12, 12) and p.r == 1
+        sys.argv = ["bench.py", "--workload", "box125-512", "--side", "10", "--tsteps", "3"]
+        p = bench.workload(bench.parse())
+        assert p.bc == "dirichlet" and p.r == 2 and p.kind == "box" and p.coeffs.shape == (5, 5, 5) and p.steps == 3
+        sys.argv = ["bench.py"]
+        p = bench.workload(bench.parse())
+        assert p.bc == "periodic" and p.shape == (8192, 8192) and p.r == 2
+    finally:
+        sys.argv = old
