@@ -9,15 +9,17 @@
 // axis, reusing every loaded shared-memory row for all outputs it feeds.
 //
 // Single grids run persistent kernels that stage their tiles with TMA:
-//  * 2D: each CTA walks its tiles with a two-stage shared-memory ring, the
-//    next tile's halo block loading (one cp.async.bulk.tensor, zero fill
-//    outside the grid = the Dirichlet halo) while the current one computes.
+//  * 2D: each CTA walks its tiles through a ring of NST shared-memory stages
+//    (four for FP32, two for FP64), the next tiles' halo blocks loading (one
+//    cp.async.bulk.tensor each, zero fill outside the grid = the Dirichlet
+//    halo) while the current one computes.
 //  * 3D (one step per launch): a work unit is a column of output planes; the
 //    CTA streams its input planes through a ring of 2r+2 plane buffers, each
 //    loaded by TMA while the planes before it are used, so every input plane
 //    is read from global memory once per unit instead of once per 3D tile.
-// With a periodic boundary, tiles whose halo crosses the grid's edge are
-// filled by the element path (indices wrapped); every other tile uses TMA.
+// With a periodic boundary, tiles (3D: planes of units) whose halo crosses
+// the grid's edge are staged by TMA like the others; then only their cells
+// outside the grid are overwritten with wrapped values (`wrap_halo_block`).
 // Waits are bounded; a timeout sets the plan's host-visible error word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -589,7 +591,7 @@ gather2d_tma_kernel(const __grid_constant__ CUtensorMap tin, const G2Args a, con
         const int s = k % NST;
         T* st_buf = stage0 + s * L.buf;
         // the stage computed at iteration k - 1 is free (barrier at its end);
-        // its generic-proxy writes (element path, sub-steps) are ordered
+        // its generic-proxy writes (halo wrap, sub-steps) are ordered
         // before the TMA write that refills it
         if (tid == 0) {
             ptx::fence_proxy_async_smem();

@@ -1,12 +1,13 @@
 """GPU parity of the TMA-staged gather kernels against the FP64 oracle.
 
 Rows that are a multiple of 16 bytes take the persistent TMA kernels: 2D
-tiles through a two-stage shared-memory ring, 3D columns of planes through a
-ring of 2r + 2 plane buffers.  The shapes span several tiles (units) with
-ragged tails in every axis; with a periodic boundary the tiles at the edges
-go through the wrapped element path and the rest through TMA.  Full-size
-grids (many tiles or units per CTA) are checked at sampled points, computed
-by the oracle on their dependency cones."""
+tiles through a ring of shared-memory stages (FP32: 32 x 128 tiles, four
+stages; FP64: 64 x 32, two), 3D columns of planes through a ring of 2r + 2
+plane buffers.  The shapes span several tiles (units) with ragged tails in
+every axis; with a periodic boundary the tiles at the edges are staged by
+TMA and then get their cells outside the grid wrapped.  Full-size grids
+(many tiles or units per CTA) are checked at sampled points, computed by the
+oracle on their dependency cones."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,7 @@ def problem(shape, r, kind, dtype, seed):
 @pytest.mark.parametrize("kind", ["star", "box"])
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
 def test_gather_tma_2d(dtype, bc, kind, r):
-    shape = (300, 516)   # 128-column and 64/32-row tiles with ragged edges
+    shape = (300, 516)   # 128- and 32-column tiles, 32- and 64-row tiles, ragged edges
     a, cg = problem(shape, r, kind, dtype, r)
     got, info = run(a, r, kind, cg, dtype, bc, 3, impl="gather")
     assert info["impl"] == 1
@@ -94,7 +95,7 @@ def test_gather_tma_2d_many_tiles_per_cta(bc):
         y = plan.apply(x, steps=steps)
         torch.cuda.synchronize()
         assert sx.stencil_plan_info(plan.handle)["device_error"] == 0
-        pts = seam_points(shape, [(64,), (128,)], 96, 1)
+        pts = seam_points(shape, [(32, 64), (128,)], 96, 1)
         got = y[tuple(torch.as_tensor(c, device="cuda") for c in pts.T)].double().cpu().numpy()
     finally:
         plan.close()
