@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "mx.h"
+#include "ptx.cuh"
 
 namespace stx {
 
@@ -75,9 +76,11 @@ __global__ void __launch_bounds__(128) periodic_edges_kernel(const float* __rest
     const int na = fr * nx;
     const int per_plane = na + (ny - fr) * ec;
     const int z = blockIdx.y;
-    // launched as a programmatic dependent of the tensor-core kernel: wait
-    // until that grid has completed and its writes are visible
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // launched as a programmatic dependent of the tensor-core kernel: let the
+    // next sweep's kernel start its set-up, then wait until the tensor-core
+    // grid has completed and its writes are visible
+    ptx::launch_dependents();
+    ptx::grid_dependency_wait();
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < per_plane; p += gridDim.x * blockDim.x) {
         int y, x;
         if (p < na) {
@@ -182,20 +185,10 @@ cudaError_t mx_periodic_edges(const MxPlan& p, const void* src, void* dst, cudaS
     const dim3 grid((unsigned)(want < cap ? want : (cap > 0 ? cap : 1)), (unsigned)nz);
     EdgeTable tab;
     memcpy(&tab, p.edge_table.data(), sizeof(tab));
-    // Programmatic stream serialization: the launch is processed while the
-    // tensor-core kernel drains, and the kernel waits for it (griddepcontrol)
-    // before touching memory.  Saves about 2 us per sweep.
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(128);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, periodic_edges_kernel, (const float*)src, (float*)dst, nz, ny, nx, p.ldx, p.r,
-                              tab);
+    // programmatic dependent: the launch is processed while the tensor-core
+    // kernel drains (about 2 us per sweep)
+    return launch_dependent(periodic_edges_kernel, grid, dim3(128), 0, s, (const float*)src, (float*)dst, nz, ny, nx,
+                            p.ldx, p.r, tab);
 }
 
 }  // namespace stx

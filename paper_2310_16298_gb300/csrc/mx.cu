@@ -267,6 +267,11 @@ mx2d_kernel(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ 
             ptx::mbar_arrive_expect_tx(bop_bar, args.bop_bytes);
             ptx::bulk_load(bops, (const unsigned char*)args.bops + (size_t)(blockIdx.x % kBopCopies) * args.bop_bytes,
                            args.bop_bytes, bop_bar);
+            // Launched as a programmatic dependent of the stream's previous
+            // kernel (the previous sweep, or its boundary-strip kernel): the
+            // set-up above (barriers, tensor memory, banded operands) overlapped
+            // its tail; the grids and the tile counter are touched only from here.
+            ptx::grid_dependency_wait();
             for (int i = 0;; ++i) {
                 const int s = i % kRawStages;
                 const uint32_t ph = (uint32_t)(i / kRawStages) & 1u;
@@ -788,8 +793,7 @@ cudaError_t mx2d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
         return cudaErrorInvalidValue;
     const KernelInfo ki = kernel_for(p.r, st->bf, operand_parts(p.prec));
     const int grid = a.tiles_total < st->num_sms ? a.tiles_total : st->num_sms;
-    ki.fn<<<grid, kThreads, ki.smem, s>>>(te, to, oe, oo, a);
-    return cudaGetLastError();
+    return launch_dependent(ki.fn, grid, kThreads, ki.smem, s, te, to, oe, oo, a);
 }
 
 }  // namespace stx

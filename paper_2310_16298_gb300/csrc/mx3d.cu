@@ -227,6 +227,8 @@ mx3d_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CU
         if (lane == 0) {
             ptx::mbar_arrive_expect_tx(bop_bar, args.bop_bytes);
             ptx::bulk_load(bops, args.bops, args.bop_bytes, bop_bar);
+            // programmatic dependent launch: grids and the unit counter only from here
+            ptx::grid_dependency_wait();
             int i = 0;
             bool ok = true;
             for (int k = 0; ok; ++k) {
@@ -757,8 +759,7 @@ cudaError_t mx3d_sweep(const MxPlan& p, const void* src, void* dst, int tb, cuda
     const int grid = a.units < st->num_sms ? a.units : st->num_sms;
     for (int k = 0; k < 12; ++k) a.sw[k] = st->sw[k];
     const int smem = smem_bytes_3d(st->nb, mma_lines3(lines3(p.r, st->star, st->hyb), st->nb), st->bf);
-    kernel3_for(p.r, st->star, st->bf, st->hyb)<<<grid, kThreads, smem, s>>>(map, map_out, a);
-    return cudaGetLastError();
+    return launch_dependent(kernel3_for(p.r, st->star, st->bf, st->hyb), grid, kThreads, smem, s, map, map_out, a);
 }
 
 }  // namespace stx

@@ -128,6 +128,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // Make generic-proxy shared-memory writes visible to the async proxy (TMA, tensor cores).
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and their memory operations are visible (a no-op for a
+// grid launched without the attribute); let dependents launch early.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
